@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU matching loop (libhm.so) on the large power-law
+hypergraph: n=10M vertices, m=20M edges, |e| ~ Zipf(2) on [2,1024], vertex
+degrees power-law (gamma=2.2), float32 weights in (0,1], kappa ~ 2.02e8.
+
+One step = one hm_match (the whole round loop, all four kernels of every
+round, as one CUDA graph) on inputs already resident in HBM.
+
+  value        kappa * rounds * steps / device time      (pins/s, whole job)
+  ms_per_step  time to maximal matching (CUDA events on the launching stream)
+  e2e          same metric through hm_solve_host from pinned HOST buffers:
+               H2D copies, hm_create, hm_match, result D2H inside the timing
+  roofline     dominant kernel: algorithmic bytes / its CUDA-event time, from
+               a replay with one event pair per kernel launch (hm_profile_match)
+  cpu_baseline the CPU oracle (single thread) on the same instance
+
+--impl reference runs the CPU oracle (the reference of this project) on a
+bounded sample of the same workload and prints the same JSON line.
+Multi-GPU: independent replicas, one instance per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "large": dict(desc="powerlaw hypergraph n=10M m=20M |e|~Zipf(2)[2,1024] gamma=2.2 f32 w in (0,1]",
+                  make=lambda seed: __import__("synth").large(seed=seed),
+                  sample=lambda seed: __import__("synth").large(seed=seed, n=50_000, m=100_000)),
+    "small": dict(desc="uniform hypergraph n=10k m=20k |e|~U{2..8} f32 w in (0,1]",
+                  make=lambda seed: __import__("synth").small(seed=seed),
+                  sample=lambda seed: __import__("synth").small(seed=seed)),
+    "unweighted": dict(desc="uniform hypergraph n=4M m=8M |e|~U{2..8} unweighted, hash priority",
+                       make=lambda seed: __import__("synth").unweighted(seed=seed),
+                       sample=lambda seed: __import__("synth").unweighted(seed=seed, n=40_000, m=80_000)),
+}
+METRIC = "pins/s (kappa*rounds/time)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="large")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(", ") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+                for name, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def kernel_bytes(stats: np.ndarray, n: int, m: int) -> dict:
+    """Algorithmic bytes per kernel kind, summed over rounds (formulas in the design doc)."""
+    ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT = range(8)
+    b = {"init": float(m * (1 + 8 + 4 + 1) + n * 8), "argmax": 0.0, "win": 0.0, "kill": 0.0,
+         "round_end": 0.0}
+    for r, row in enumerate(stats):
+        row = row.astype(np.float64)
+        if r == 0:
+            b["argmax"] += row[ACT] * 16 + row[PROP] * (8 + 4 + 8) + row[NEXT] * 4
+        else:
+            b["argmax"] += (row[ACT] * (4 + 8 + 4 + 1) + row[ADV] * (4 + 1)
+                            + row[PROP] * (8 + 8 + 8) + row[NEXT] * 4)
+        b["win"] += row[WIN] * (4 + 16 + 4 + 1) + row[WPIN] * (4 + 8 + 16 + 4 + 8) + row[ITEM] * 16
+        b["kill"] += row[ITEM] * 16 + row[KILL] * (4 + 1)
+    return b
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def cpu_cores_used() -> int:
+    return 1
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload]
+    h = wl["sample"](args.seed)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.match(h)
+    t0 = time.perf_counter()
+    rounds = 0
+    for _ in range(args.steps):
+        rounds = oracle.match(h).rounds
+    dt = time.perf_counter() - t0
+    value = h.kappa * rounds * args.steps / dt
+    sample = f"{h.name}: kappa={h.kappa}, rounds={rounds}, one oracle run per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "pins/s", "cores": cpu_cores_used(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_2602_22976_gb300 as hm
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hm.build()
+    wl = WORKLOADS[args.workload]
+    h = wl["make"](args.seed)
+    mt = hm.Matcher.from_hypergraph(h)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(max(args.warmup, 3)):
+        mt.match(stream)
+    res = mt.result()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps, outside the step's events
+        starts[k].record(stream)
+        mt.match(stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = float(sum(step_ms))
+    res2 = mt.result()
+    assert res2.rounds == res.rounds and res2.count == res.count
+    units = float(h.kappa) * res.rounds * args.steps
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([units, t_ms], dtype=torch.float64, device="cuda")
+        u = tt[0:1].clone()
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        tm = tt[1:2].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        units, t_max = float(u.item()), float(tm.item())
+    value = units / (t_max / 1e3)
+
+    # per-kernel replay for the roofline
+    prof = mt.profile(stream)
+    stats = mt.round_stats()
+    create_ms = mt.create_ms()
+    kb = kernel_bytes(stats, h.n, h.m)
+    dom = max(("argmax", "win", "kill"), key=lambda k: prof[k][0])
+    peaks = measured_peaks()
+    achieved = kb[dom] / (prof[dom][0] / 1e3) / 1e9
+    per_kernel = {k: {"ms": prof[k][0], "launches": prof[k][1], "alg_bytes": kb[k],
+                      "gbs": (kb[k] / (prof[k][0] / 1e3) / 1e9) if prof[k][0] > 0 else None}
+                  for k in prof}
+    total_bytes = sum(kb.values())
+    rounds_run = int(prof["argmax"][1])
+    launches = 1 + 4 * rounds_run
+
+    out = {}
+    if rank == 0:
+        # end to end through hm_solve_host from pinned host memory
+        e2e = None
+        if args.e2e_steps > 0:
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            eoff_p, pins_p = pin(h.eoff), pin(h.pins)
+            w_p = None if h.weights is None else pin(h.weights)
+            edges_p = torch.empty(max(h.m, 1), dtype=torch.int32).pin_memory()
+            flags = hm.HM_UNWEIGHTED if h.weights is None else 0
+            sh = stream.cuda_stream or None
+            call = lambda: hm.solve_host_ptrs(h.n, h.m, eoff_p.data_ptr(), pins_p.data_ptr(),
+                                              None if w_p is None else w_p.data_ptr(), h.seed,
+                                              flags, edges_p.data_ptr(), sh)
+            call()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                cnt, rnd, _w = call()
+            torch.cuda.synchronize()
+            te = (time.perf_counter() - t0) / args.e2e_steps
+            assert rnd == res.rounds and cnt == res.count
+            h2d = h.eoff.nbytes + h.pins.nbytes + (0 if h.weights is None else h.weights.nbytes)
+            e2e = {"value": h.kappa * res.rounds / te, "unit": "pins/s", "ms_per_step": te * 1e3,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 8 + 64)}
+        cpu = None
+        parity = None
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            o = oracle.match(h)
+            tc = time.perf_counter() - t0
+            parity = bool(np.array_equal(o.edges, res.edges) and o.rounds == res.rounds)
+            cpu = {"value": h.kappa * o.rounds / tc, "unit": "pins/s", "cores": cpu_cores_used(),
+                   "kind": "oracle", "sample": f"the full instance, one oracle run ({tc:.1f} s)",
+                   "active_pins": int(o.round_stats[:, 1].sum())}
+        out = {
+            "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": h.n, "m": h.m, "kappa": h.kappa,
+                       "rounds": res.rounds, "matched": res.count, "weight": res.weight,
+                       "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps, outside step events",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_matching_ms": {"mean": t_ms / args.steps, "median": statistics.median(step_ms),
+                                    "p99": float(np.percentile(step_ms, 99))},
+            "create_ms": create_ms,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": peaks["source"],
+                         "loop_gbs": total_bytes / (sum(v[0] for v in prof.values()) / 1e3) / 1e9},
+            "kernels": per_kernel,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches * args.steps,
+            "parity_vs_oracle": parity,
+        }
+        if cpu and cpu.get("active_pins"):
+            out["active_pins_per_s"] = cpu["active_pins"] * args.steps * world / (t_max / 1e3)
+        print(json.dumps(out), flush=True)
+    mt.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * hm.h - C ABI of the GB300 (sm_103a) locally-maximal hypergraph matching
+ * library (libhm.so).
+ *
+ * Method: "Efficient Parallel Algorithms for Hypergraph Matching"
+ * (Reinstaedtler, Schulz, Sitchinava, Walliser). A weighted hypergraph
+ * H = (V, E, w) with w > 0 (Sec. 2.1) is matched in rounds (Sec. 3.1,
+ * Alg. 1, Alg. 3): every vertex takes its highest-priority live incident
+ * edge, every live edge chosen by all of its vertices joins the matching M,
+ * and every live edge touching a vertex of a new matching edge is
+ * deactivated; rounds repeat until no edge is live. The result is a maximal
+ * matching with w(M) >= OPT/d (Lemma 1).
+ *
+ * Order on edges. The paper re-draws random weights before every round
+ * (Sec. 3.1, Sec. 5.1). This library fixes one strict total order for the
+ * whole run instead, which makes the result unique:
+ *   weighted:   heavier edge first; equal weight -> smaller edge id first;
+ *   unweighted: priority fmix32(e ^ s), s = low 32 bits of the first
+ *               SplitMix64 output for `seed` (MurmurHash3 finaliser, Appleby;
+ *               SplitMix64, Steele/Lea/Flood 2014). fmix32 is a bijection,
+ *               so the order is strict.
+ * Under a fixed order the matching equals the sequential greedy matching
+ * (sort by priority, take an edge when all its vertices are free; the
+ * paper's Greedy baseline, Sec. 5.2).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an hm_status. On failure hm_last_error() returns a
+ *    thread-local, NUL-terminated message describing the first problem.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it in stream order.
+ *  - Device pointers must be device-accessible memory of the current CUDA
+ *    device; host pointers must be ordinary host memory unless stated.
+ *  - A handle is bound to the device that was current at hm_create.
+ *  - No entry point traps or aborts on bad input; nothing is printed.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_handle hm_handle;
+
+typedef enum {
+    HM_OK = 0,
+    HM_EINVAL = 1,    /* invalid argument or invalid hypergraph */
+    HM_ENOMEM = 2,    /* a device or host allocation failed */
+    HM_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    HM_ETIMEOUT = 4,  /* the round cap stopped the loop before it finished */
+    HM_EBUSY = 5      /* a match on this handle is still running on another stream */
+} hm_status;
+
+/* hm_create flags */
+#define HM_UNWEIGHTED   0x1u  /* ignore weights (may be NULL); priority = fmix32(e ^ s) */
+#define HM_BORROW_INPUT 0x2u  /* accepted for compatibility: inputs are never kept (see hm_create) */
+#define HM_VALIDATE     0x4u  /* accepted for compatibility: full validation always runs */
+
+/*
+ * hm_create - build a matching handle for one hypergraph.
+ *
+ * Input (edge CSR, the E_id/E_p pair of Sec. 4.1): edge e (0 <= e < m) has
+ * the vertices pins[eoff[e] .. eoff[e+1]-1]; kappa = eoff[m] (Sec. 2.1:
+ * kappa = sum of edge sizes = sum of degrees).
+ *   n        number of vertices, 0 <= n <= 2^31-1 (degree-0 vertices allowed)
+ *   m        number of edges,    0 <= m <= 2^31-1
+ *   eoff     DEVICE int64[m+1], eoff[0] == 0, strictly increasing (no empty
+ *            edge), eoff[m] = kappa <= 2^32-1
+ *   pins     DEVICE int32[kappa], every value in [0, n), no vertex twice in
+ *            one edge (edges are sets, Sec. 2.1)
+ *   weights  DEVICE float32[m], every weight finite and > 0 (Sec. 2.1);
+ *            ignored and may be NULL with HM_UNWEIGHTED
+ *   seed     priority seed for HM_UNWEIGHTED, otherwise unused
+ *   flags    HM_UNWEIGHTED | HM_BORROW_INPUT | HM_VALIDATE
+ *   out      receives the handle (set to NULL on failure)
+ *
+ * Work: validates the input on the device, fixes the order on edges,
+ * relabels edges by decreasing priority and builds the vertex CSR (V_id/V_p,
+ * Sec. 4.1) with every vertex's edges in decreasing priority. All of it is
+ * preprocessing, excluded from match time like the paper's load and
+ * transfer time (Sec. 5.1).
+ *
+ * Ownership: the inputs are only read; they may be freed or changed once
+ * hm_create returns (it synchronises `cuda_stream` before returning). The
+ * handle owns all device memory it allocates (stream-ordered, on
+ * `cuda_stream`) until hm_destroy.
+ *
+ * Errors: HM_EINVAL for n, m out of range, NULL pointers, eoff[0] != 0,
+ * kappa out of range, an empty or decreasing edge range, a pin outside
+ * [0, n), a vertex repeated inside an edge, a weight that is not finite or
+ * is <= 0 (including -0.0), or NULL weights without HM_UNWEIGHTED;
+ * HM_ENOMEM; HM_ECUDA.
+ */
+hm_status hm_create(hm_handle **out, int64_t n, int64_t m,
+                    const int64_t *eoff, const int32_t *pins, const float *weights,
+                    uint64_t seed, uint32_t flags, void *cuda_stream);
+
+/*
+ * hm_match - enqueue the whole round loop (Alg. 1 / Alg. 3 rounds until no
+ * edge is live, Sec. 3.1) on `cuda_stream`; returns without waiting.
+ * The loop runs on the device as one CUDA graph with a conditional while
+ * node; no host round trip happens between rounds. A handle can be matched
+ * any number of times; every call recomputes the same result from scratch.
+ * Errors: HM_EINVAL (NULL handle), HM_EBUSY (a match of this handle is still
+ * running on a different stream), HM_ECUDA. Loop outcomes (round cap,
+ * detected inconsistency) are reported by hm_result.
+ */
+hm_status hm_match(hm_handle *h, void *cuda_stream);
+
+/*
+ * hm_set_round_cap - stop the loop after at most `cap` rounds (cap >= 1).
+ * The default cap is m + 1, which no valid input reaches: under a strict
+ * order the best live edge wins every round, so at most m rounds run.
+ * Errors: HM_EINVAL.
+ */
+hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
+
+/*
+ * hm_result - wait for the last hm_match and report its result.
+ *   edges_out   HOST int32[m] or NULL: the matched edge ids, ascending
+ *               (input numbering)
+ *   count_out   HOST, may be NULL: |M|
+ *   rounds_out  HOST, may be NULL: rounds that started with a live edge
+ *   weight_out  HOST, may be NULL: w(M) summed in float64 in ascending edge
+ *               id order (|M| for unweighted handles)
+ * Errors: HM_EINVAL (NULL handle, no match run yet), HM_ETIMEOUT (the round
+ * cap stopped the loop; outputs then describe the partial matching),
+ * HM_EINVAL with message "duplicate pin" if a round found no winner while
+ * vertices still had live edges (impossible for valid input), HM_ECUDA.
+ */
+hm_status hm_result(hm_handle *h, int32_t *edges_out, int64_t *count_out,
+                    int32_t *rounds_out, double *weight_out);
+
+/*
+ * hm_result_device - enqueue on `cuda_stream` a copy of the membership mask
+ * of the last match into DEVICE uint8[m] `in_matching` (1 = e in M), input
+ * edge numbering. Does not wait. Errors: HM_EINVAL, HM_ECUDA.
+ */
+hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream);
+
+/*
+ * hm_round_stats - per-round counters of the last match (waits for it).
+ * For round r (0-based, r < min(rounds_cap, 4096)) row r of HOST
+ * int64[max_rounds][HM_STATS_COLS] receives:
+ */
+#define HM_STAT_ACTIVE    0  /* vertices visited by the argmax step */
+#define HM_STAT_ADVANCE   1  /* adjacency entries skipped by the argmax step */
+#define HM_STAT_PROPOSALS 2  /* vertices that chose a new best edge */
+#define HM_STAT_WINNERS   3  /* edges that joined M */
+#define HM_STAT_WINPINS   4  /* sum of |e| over those edges */
+#define HM_STAT_KILLS     5  /* adjacency entries deactivated by the kill step */
+#define HM_STAT_ITEMS     6  /* kill work items (chunks) */
+#define HM_STAT_NEXT      7  /* vertices kept for the next round */
+#define HM_STATS_COLS     8
+/* Returns the number of rows written in *rows_out. Errors: HM_EINVAL. */
+hm_status hm_round_stats(hm_handle *h, int64_t *stats, int32_t max_rounds, int32_t *rows_out);
+
+/*
+ * hm_vertex_state - per-vertex state after the last match (waits for it),
+ * into HOST int32[n]: the input id of the vertex's current best edge, or
+ * HM_VERTEX_MATCHED if the vertex is covered by M, or HM_VERTEX_NONE if it
+ * has no live edge (or degree 0). After a match stopped by a round cap of r
+ * this is T[v] of round r (Alg. 3) for unmatched vertices.
+ */
+#define HM_VERTEX_MATCHED (-1)
+#define HM_VERTEX_NONE    (-2)
+hm_status hm_vertex_state(hm_handle *h, int32_t *best_edge_out);
+
+/*
+ * hm_profile_match - run one match with the rounds driven from the host,
+ * one launch per kernel with a CUDA event pair around every launch on
+ * `cuda_stream`, and report per kernel kind k (HM_K_*):
+ *   ms_out[k]        summed device time of its launches (CUDA events)
+ *   launches_out[k]  number of launches
+ * The result equals hm_match's. Waits for completion. Used to measure each
+ * kernel; hm_match is the production path. Errors: as hm_match.
+ */
+#define HM_K_INIT    0  /* per-match state reset */
+#define HM_K_ARGMAX  1  /* a1: vertex argmax (cursor advance) + proposals */
+#define HM_K_WIN     2  /* a2: winners join M, their vertices are marked */
+#define HM_K_KILL    3  /* a3: deactivate edges of newly matched vertices */
+#define HM_K_ROUND   4  /* a4: round bookkeeping, termination test */
+#define HM_K_COUNT   5
+hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int64_t *launches_out);
+
+/*
+ * hm_create_ms - device time of the hm_create phases of this handle
+ * (CUDA events): [0] validation, [1] priority sort, [2] edge relabel,
+ * [3] vertex CSR build, [4] total. HOST double[5]. Errors: HM_EINVAL.
+ */
+hm_status hm_create_ms(hm_handle *h, double *ms_out);
+
+/*
+ * hm_solve_host - one call from HOST buffers to HOST result: copies eoff,
+ * pins, weights (host memory; pinned memory gives full link bandwidth) to
+ * the device on `cuda_stream`, runs hm_create + hm_match + hm_result and
+ * frees everything. Arguments as hm_create and hm_result (edges_out is
+ * HOST int32[m] or NULL). Errors: union of those calls.
+ */
+hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
+                        const float *weights, uint64_t seed, uint32_t flags,
+                        int32_t *edges_out, int64_t *count_out, int32_t *rounds_out,
+                        double *weight_out, void *cuda_stream);
+
+/* hm_last_error - message of the last failure on this thread ("" if none). */
+const char *hm_last_error(void);
+
+/* hm_destroy - wait for outstanding work of the handle and free it. NULL is a no-op. */
+void hm_destroy(hm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H */

@@ -1,0 +1,357 @@
+// api.cu - the extern "C" entry points declared in include/hm.h.
+#include "hm_internal.cuh"
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace hm {
+
+namespace {
+thread_local std::string g_err;
+
+bool device_pointer(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+hm_status einval(const char *msg) {
+    g_err = msg;
+    return HM_EINVAL;
+}
+
+hm_status check_device(const Handle *h) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != h->device) return einval("the current CUDA device is not the handle's device");
+    return HM_OK;
+}
+
+// Waits for the last match and copies the loop state to the host.
+hm_status wait_state(Handle *h) {
+    if (!h->matched_once) return einval("no match has been run on this handle");
+    cudaError_t e = cudaEventSynchronize(h->done);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the match");
+    e = cudaMemcpy(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the loop state");
+    return HM_OK;
+}
+
+hm_status loop_status(const Handle *h) {
+    switch (h->h_st->status) {
+    case HM_OK:
+        return HM_OK;
+    case HM_ETIMEOUT:
+        g_err = "round cap reached before the loop finished";
+        return HM_ETIMEOUT;
+    case HM_EINVAL:
+        g_err = "duplicate pin: a round found no winner while vertices still had live edges";
+        return HM_EINVAL;
+    default: {
+        char buf[120];
+        snprintf(buf, sizeof buf, "internal consistency check failed in the round loop (code %d)",
+                 h->h_st->fault);
+        g_err = buf;
+        return HM_ECUDA;
+    }
+    }
+}
+
+void raise_pool_threshold(int dev) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+}
+}  // namespace
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+hm_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();
+    return HM_ECUDA;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+const char *hm_last_error(void) { return g_err.c_str(); }
+
+void hm_destroy(hm_handle *hh) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return;
+    if (h->done) cudaEventSynchronize(h->done);
+    if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
+    free_handle_buffers(h);
+    delete h;
+}
+
+hm_status hm_create(hm_handle **out, int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
+                    const float *weights, uint64_t seed, uint32_t flags, void *cuda_stream) {
+    if (!out) return einval("out is NULL");
+    *out = nullptr;
+    if (flags & ~(HM_UNWEIGHTED | HM_BORROW_INPUT | HM_VALIDATE)) return einval("unknown flag bits");
+    if (n < 0 || n > INT32_MAX) return einval("n must be in [0, 2^31-1]");
+    if (m < 0 || m > INT32_MAX) return einval("m must be in [0, 2^31-1]");
+    const bool weighted = !(flags & HM_UNWEIGHTED);
+    if (!eoff) return einval("eoff is NULL");
+    if (!device_pointer(eoff)) return einval("eoff must be device memory");
+    if (m > 0 && weighted) {
+        if (!weights) return einval("weights is NULL without HM_UNWEIGHTED");
+        if (!device_pointer(weights)) return einval("weights must be device memory");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int64_t ends[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&ends[0], eoff, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&ends[1], eoff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading eoff[0], eoff[m]");
+    if (ends[0] != 0) return einval("eoff[0] must be 0");
+    if (ends[1] < m) return einval("eoff[m] < m: some edge is empty or eoff decreases");
+    if ((uint64_t)ends[1] > 0xFFFFFFFFull) return einval("kappa = eoff[m] must be <= 2^32-1");
+    if (ends[1] > 0) {
+        if (!pins) return einval("pins is NULL");
+        if (!device_pointer(pins)) return einval("pins must be device memory");
+    }
+    if (m > 0 && n == 0) return einval("edges need vertices: n == 0 with m > 0");
+
+    Handle *h = new (std::nothrow) Handle();
+    if (!h) return HM_ENOMEM;
+    h->n = n;
+    h->m = m;
+    h->kappa = (uint64_t)ends[1];
+    h->weighted = weighted;
+    h->seed = seed;
+    h->cap = m + 1;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    raise_pool_threshold(h->device);
+    hm_status st = create_structures(h, eoff, pins, weights, s);
+    if (st == HM_OK) st = alloc_round_state(h, s);
+    if (st == HM_OK) {
+        if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess)
+            st = cuda_fail(e, "cudaEventCreate");
+    }
+    if (st == HM_OK) {
+        if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            st = cuda_fail(e, "cudaStreamCreate");
+    }
+    if (st == HM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "hm_create");
+    if (st != HM_OK) {
+        cudaStreamSynchronize(s);
+        hm_destroy(reinterpret_cast<hm_handle *>(h));
+        return st;
+    }
+    *out = reinterpret_cast<hm_handle *>(h);
+    return HM_OK;
+}
+
+hm_status hm_set_round_cap(hm_handle *hh, int64_t cap) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (cap < 1) return einval("round cap must be >= 1");
+    h->cap = cap;
+    return HM_OK;
+}
+
+static hm_status busy_check(Handle *h, cudaStream_t s) {
+    if (h->matched_once && s != h->last_stream && cudaEventQuery(h->done) == cudaErrorNotReady)
+        return HM_EBUSY;
+    cudaGetLastError();
+    return HM_OK;
+}
+
+hm_status hm_match(hm_handle *hh, void *cuda_stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    hm_status st = check_device(h);
+    if (st != HM_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (busy_check(h, s) != HM_OK) {
+        g_err = "a match of this handle is still running on another stream";
+        return HM_EBUSY;
+    }
+    st = launch_match_graph(h, s);
+    if (st != HM_OK) return st;
+    cudaError_t e = cudaEventRecord(h->done, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    h->last_stream = s;
+    h->matched_once = true;
+    return HM_OK;
+}
+
+hm_status hm_profile_match(hm_handle *hh, void *cuda_stream, double *ms_out, int64_t *launches_out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (!ms_out || !launches_out) return einval("output pointer is NULL");
+    hm_status st = check_device(h);
+    if (st != HM_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (busy_check(h, s) != HM_OK) {
+        g_err = "a match of this handle is still running on another stream";
+        return HM_EBUSY;
+    }
+    st = profile_match(h, s, ms_out, launches_out);
+    h->last_stream = s;
+    h->matched_once = true;
+    return st;
+}
+
+hm_status hm_result(hm_handle *hh, int32_t *edges_out, int64_t *count_out, int32_t *rounds_out,
+                    double *weight_out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    hm_status st = wait_state(h);
+    if (st != HM_OK) return st;
+    cudaStream_t s = h->cap_stream;
+    const uint64_t m = (uint64_t)h->m;
+    cudaError_t e = compact_flags(h->inM, m, h->weighted ? h->weights : nullptr, h->res_idx, h->res_w,
+                                  h->res_part, s);
+    uint32_t count = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&count, h->res_part + compact_scratch_elems(m), sizeof count,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "result compaction");
+    if (edges_out && count)
+        if ((e = cudaMemcpy(edges_out, h->res_idx, (size_t)count * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "result copy");
+    if (weight_out) {
+        if (!h->weighted) {
+            *weight_out = (double)count;
+        } else {
+            std::vector<float> w(count);
+            if (count &&
+                (e = cudaMemcpy(w.data(), h->res_w, (size_t)count * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return cuda_fail(e, "result weights");
+            double acc = 0.0;
+            for (uint32_t i = 0; i < count; ++i) acc += (double)w[i];  // ascending edge id
+            *weight_out = acc;
+        }
+    }
+    if (count_out) *count_out = count;
+    if (rounds_out) *rounds_out = h->h_st->rounds_done;
+    return loop_status(h);
+}
+
+hm_status hm_result_device(hm_handle *hh, uint8_t *in_matching, void *cuda_stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (!in_matching) return einval("in_matching is NULL");
+    if (!h->matched_once) return einval("no match has been run on this handle");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamWaitEvent(s, h->done, 0);
+    if (e == cudaSuccess && h->m)
+        e = cudaMemcpyAsync(in_matching, h->inM, (size_t)h->m, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hm_result_device");
+    return HM_OK;
+}
+
+hm_status hm_round_stats(hm_handle *hh, int64_t *stats, int32_t max_rounds, int32_t *rows_out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (!stats || !rows_out || max_rounds < 0) return einval("bad output arguments");
+    hm_status st = wait_state(h);
+    if (st != HM_OK) return st;
+    int32_t rows = h->h_st->round;
+    if (rows > kStatRounds) rows = kStatRounds;
+    if (rows > max_rounds) rows = max_rounds;
+    if (rows > 0) {
+        cudaError_t e = cudaMemcpy(stats, h->stats, (size_t)rows * HM_STATS_COLS * sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "hm_round_stats");
+    }
+    *rows_out = rows;
+    return HM_OK;
+}
+
+hm_status hm_vertex_state(hm_handle *hh, int32_t *best_edge_out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (!best_edge_out) return einval("best_edge_out is NULL");
+    hm_status st = wait_state(h);
+    if (st != HM_OK) return st;
+    if (h->n == 0) return HM_OK;
+    cudaStream_t s = h->cap_stream;
+    int32_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d, (size_t)h->n * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hm_vertex_state alloc");
+    e = launch_vertex_state(h, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best_edge_out, d, (size_t)h->n * 4, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "hm_vertex_state");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "hm_vertex_state");
+    return HM_OK;
+}
+
+hm_status hm_create_ms(hm_handle *hh, double *ms_out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (!ms_out) return einval("ms_out is NULL");
+    memcpy(ms_out, h->create_ms, sizeof h->create_ms);
+    return HM_OK;
+}
+
+hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
+                        const float *weights, uint64_t seed, uint32_t flags, int32_t *edges_out,
+                        int64_t *count_out, int32_t *rounds_out, double *weight_out, void *cuda_stream) {
+    if (n < 0 || m < 0 || m > INT32_MAX || n > INT32_MAX) return einval("n, m must be in [0, 2^31-1]");
+    if (!eoff) return einval("eoff is NULL");
+    const bool weighted = !(flags & HM_UNWEIGHTED);
+    if (m > 0 && weighted && !weights) return einval("weights is NULL without HM_UNWEIGHTED");
+    const int64_t kappa = eoff[m];
+    if (eoff[0] != 0 || kappa < 0 || (uint64_t)kappa > 0xFFFFFFFFull)
+        return einval("eoff[0] must be 0 and eoff[m] in [0, 2^32-1]");
+    if (kappa > 0 && !pins) return einval("pins is NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    raise_pool_threshold(dev);
+    int64_t *d_eoff = nullptr;
+    int32_t *d_pins = nullptr;
+    float *d_w = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_eoff, (size_t)(m + 1) * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_pins, (size_t)(kappa > 0 ? kappa : 1) * 4, s);
+    if (e == cudaSuccess && weighted) e = cudaMallocAsync((void **)&d_w, (size_t)(m > 0 ? m : 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_eoff, eoff, (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && kappa > 0)
+        e = cudaMemcpyAsync(d_pins, pins, (size_t)kappa * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && weighted && m > 0)
+        e = cudaMemcpyAsync(d_w, weights, (size_t)m * 4, cudaMemcpyHostToDevice, s);
+    hm_status st = HM_OK;
+    if (e != cudaSuccess) st = cuda_fail(e, "hm_solve_host upload");
+    hm_handle *h = nullptr;
+    if (st == HM_OK) st = hm_create(&h, n, m, d_eoff, d_pins, d_w, seed, flags, cuda_stream);
+    // inputs are no longer needed once hm_create returned
+    if (d_eoff) cudaFreeAsync(d_eoff, s);
+    if (d_pins) cudaFreeAsync(d_pins, s);
+    if (d_w) cudaFreeAsync(d_w, s);
+    if (st == HM_OK) st = hm_match(h, cuda_stream);
+    if (st == HM_OK) st = hm_result(h, edges_out, count_out, rounds_out, weight_out);
+    if (h) {
+        std::string keep = g_err;
+        hm_destroy(h);
+        g_err = keep;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+// create.cu - builds a handle's device structures from the edge CSR.
+//
+//  1. validate the input (Sec. 2.1: edges are non-empty vertex sets, weights
+//     are positive reals);
+//  2. fix the strict order on edges and relabel edges by decreasing priority
+//     (j = 0 is the best edge): a stable radix sort of the complemented
+//     32-bit priority over edges taken in increasing id, so equal priorities
+//     keep the smaller id first;
+//  3. copy the pins into j order (E_id/E_p of Sec. 4.1);
+//  4. build the vertex CSR (V_id/V_p of Sec. 4.1) by a stable radix sort of
+//     the (vertex, j) pairs by vertex: every vertex's list comes out in
+//     ascending j, i.e. decreasing priority, which turns the per-vertex argmax
+//     of every round (Alg. 1 / Alg. 3) into a forward-only cursor. A vertex
+//     repeated inside an edge shows up as two equal neighbours in that list.
+#include "hm_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace hm {
+namespace {
+
+constexpr int kT = 256;
+
+enum : uint32_t { kErrEdgeRange = 1u, kErrPin = 2u, kErrWeight = 4u, kErrDup = 8u };
+
+struct CreateErr {
+    uint32_t flags;
+    uint32_t pad;
+    unsigned long long first[4];  // first offending index per error kind
+};
+
+__device__ __forceinline__ void report(CreateErr *err, uint32_t kind, int bit, unsigned long long idx) {
+    atomicOr(&err->flags, kind);
+    atomicMin(&err->first[bit], idx);
+}
+
+// Sec. 2.1: every edge is a non-empty set, weights are positive.
+__global__ void k_validate(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
+                           const float *__restrict__ w, int64_t n, int64_t m, uint64_t kappa,
+                           CreateErr *err) {
+    const uint64_t total = (uint64_t)(m > (int64_t)kappa ? m : (int64_t)kappa);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (i < (uint64_t)m) {
+            if (eoff[i + 1] <= eoff[i]) report(err, kErrEdgeRange, 0, i);
+            if (w) {
+                const uint32_t b = __float_as_uint(w[i]);
+                // finite and > 0: sign clear, not zero, exponent below all-ones
+                if (b == 0u || b >= 0x7F800000u) report(err, kErrWeight, 2, i);
+            }
+        }
+        if (i < kappa) {
+            const int32_t p = pins[i];
+            if (p < 0 || (int64_t)p >= n) report(err, kErrPin, 1, i);
+        }
+    }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): first output for a given seed.
+__host__ __device__ inline uint64_t splitmix64_first(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+// MurmurHash3 32-bit finaliser (Appleby): a bijection on 32-bit words.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Sort key = complemented priority (ascending sort = decreasing priority).
+// Positive finite floats order like their bit patterns.
+__global__ void k_priority(const float *__restrict__ w, uint32_t salt, int64_t m,
+                           uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t prio = w ? __float_as_uint(w[e]) : fmix32((uint32_t)e ^ salt);
+        key[e] = ~prio;
+        val[e] = (uint32_t)e;
+    }
+}
+
+__global__ void k_sizes_j(const int64_t *__restrict__ eoff, const uint32_t *__restrict__ order,
+                          int64_t m, int64_t *__restrict__ szj) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = order[j];
+        szj[j] = eoff[e + 1] - eoff[e];
+    }
+}
+
+// Warp per edge: pins of input edge order[j] -> pinsj at eoffj[j]; the
+// matching slots of jval receive j.
+__global__ void k_relabel(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
+                          const uint32_t *__restrict__ order, const int64_t *__restrict__ eoffj,
+                          int64_t m, int32_t *__restrict__ pinsj, uint32_t *__restrict__ jval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp; j < m; j += nwarps) {
+        const uint32_t e = order[j];
+        const int64_t src = eoff[e], dst = eoffj[j], len = eoffj[j + 1] - dst;
+        for (int64_t t = lane; t < len; t += 32) {
+            pinsj[dst + t] = pins[src + t];
+            jval[dst + t] = (uint32_t)j;
+        }
+    }
+}
+
+// voff from the vertex-sorted pin list: position i starts the segments of
+// the vertices (sv[i-1], sv[i]] (degree-0 vertices get empty segments).
+// Also flags a vertex repeated inside one edge (equal (v, j) neighbours).
+__global__ void k_voff(const uint32_t *__restrict__ sv, const uint32_t *__restrict__ vadj,
+                       uint64_t kappa, int64_t n, int64_t *__restrict__ voff, CreateErr *err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= kappa;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = i == 0 ? 0 : (int64_t)sv[i - 1] + 1;
+        const int64_t hi = i == kappa ? n : (int64_t)sv[i];
+        for (int64_t v = lo; v <= hi; ++v) voff[v] = (int64_t)i;
+        if (i > 0 && i < kappa && sv[i] == sv[i - 1] && vadj[i] == vadj[i - 1])
+            report(err, kErrDup, 3, i);
+    }
+}
+
+template <typename T>
+hm_status dalloc(T **p, uint64_t count, cudaStream_t s, const char *what) {
+    cudaError_t e = cudaMallocAsync((void **)p, (size_t)std::max<uint64_t>(count, 1) * sizeof(T), s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof buf, "out of device memory allocating %s (%llu bytes)", what,
+                 (unsigned long long)(count * sizeof(T)));
+        set_error(buf);
+        return HM_ENOMEM;
+    }
+    return HM_OK;
+}
+
+template <typename T>
+void dfree(T *&p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+}
+
+int bit_width(uint64_t x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+}  // namespace
+
+// Frees every registered temporary (stream-ordered) when it goes out of scope.
+struct Temps {
+    cudaStream_t s;
+    void *p[16] = {};
+    int k = 0;
+    explicit Temps(cudaStream_t st) : s(st) {}
+    template <typename T>
+    hm_status get(T **out, uint64_t count, const char *what) {
+        hm_status st = dalloc(out, count, s, what);
+        if (st == HM_OK) p[k++] = *out;
+        return st;
+    }
+    template <typename T>
+    void drop(T *&q) {
+        for (int i = 0; i < k; ++i)
+            if (p[i] == q) {
+                cudaFreeAsync(p[i], s);
+                p[i] = nullptr;
+            }
+        q = nullptr;
+    }
+    ~Temps() {
+        for (int i = 0; i < k; ++i)
+            if (p[i]) cudaFreeAsync(p[i], s);
+    }
+};
+
+hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
+                            const float *weights, cudaStream_t s) {
+    const int64_t n = h->n, m = h->m;
+    const uint64_t kappa = h->kappa;
+    struct Events {
+        cudaEvent_t e[5] = {};
+        ~Events() {
+            for (auto &x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    for (auto &e : ev.e)
+        if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+
+    Temps tmp(s);
+    hm_status st;
+    const uint64_t big = std::max<uint64_t>((uint64_t)m, kappa);
+    const unsigned gbig = grid_for(big, kT, h->sm_count, 16);
+    const unsigned gm = grid_for((uint64_t)m, kT, h->sm_count, 16);
+
+    CreateErr *derr = nullptr;
+    if ((st = tmp.get(&derr, 1, "error word")) != HM_OK) return st;
+    CreateErr init{};
+    init.first[0] = init.first[1] = init.first[2] = init.first[3] = ~0ull;
+    CreateErr herr{};
+    cudaEventRecord(ev.e[0], s);
+    cudaError_t ce = cudaMemcpyAsync(derr, &init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "error word upload");
+
+    // 1. validation
+    k_validate<<<gbig, kT, 0, s>>>(eoff, pins, h->weighted ? weights : nullptr, n, m, kappa, derr);
+    cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
+    ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "validation");
+    if (herr.flags) {
+        char buf[200];
+        if (herr.flags & kErrEdgeRange)
+            snprintf(buf, sizeof buf,
+                     "eoff is not strictly increasing at edge %llu (empty or decreasing edge)",
+                     herr.first[0]);
+        else if (herr.flags & kErrPin)
+            snprintf(buf, sizeof buf, "pin at position %llu is outside [0, n)", herr.first[1]);
+        else
+            snprintf(buf, sizeof buf, "weight of edge %llu is not finite and > 0", herr.first[2]);
+        set_error(buf);
+        return HM_EINVAL;
+    }
+    cudaEventRecord(ev.e[1], s);
+
+    // 2. order on edges: stable sort of ~priority over edges in id order
+    uint32_t *key = nullptr, *val = nullptr, *tk = nullptr, *tv = nullptr, *sk = nullptr,
+             *order_u = nullptr, *rscratch = nullptr;
+    if ((st = tmp.get(&key, big, "sort keys")) != HM_OK ||
+        (st = tmp.get(&val, big, "sort values")) != HM_OK ||
+        (st = tmp.get(&tk, big, "sort keys (alt)")) != HM_OK ||
+        (st = tmp.get(&tv, big, "sort values (alt)")) != HM_OK ||
+        (st = tmp.get(&sk, (uint64_t)m, "sorted priorities")) != HM_OK ||
+        (st = tmp.get(&rscratch, radix_scratch_elems(big), "sort scratch")) != HM_OK ||
+        (st = dalloc(&order_u, (uint64_t)m, s, "order")) != HM_OK)
+        return st;
+    h->order = (int32_t *)order_u;  // owned by the handle from here on
+    const uint32_t salt = (uint32_t)splitmix64_first(h->seed);
+    k_priority<<<gm, kT, 0, s>>>(h->weighted ? weights : nullptr, salt, m, key, val);
+    ce = radix_sort_pairs(key, val, sk, order_u, tk, tv, (uint64_t)m, 32, rscratch, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "priority sort");
+    tmp.drop(sk);
+    cudaEventRecord(ev.e[2], s);
+
+    // 3. edge CSR in j order
+    int64_t *szj = nullptr, *i64scratch = nullptr;
+    if ((st = dalloc(&h->eoffj, (uint64_t)m + 1, s, "eoffj")) != HM_OK ||
+        (st = dalloc(&h->pinsj, kappa, s, "pinsj")) != HM_OK ||
+        (st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
+        (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
+        return st;
+    k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj);
+    ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
+    tmp.drop(szj);
+    tmp.drop(i64scratch);
+    // val now receives j for every pin slot; the relabelled pins double as
+    // the keys of the vertex sort
+    k_relabel<<<grid_for((uint64_t)m * 32, kT, h->sm_count, 16), kT, 0, s>>>(
+        eoff, pins, order_u, h->eoffj, m, h->pinsj, val);
+    cudaEventRecord(ev.e[3], s);
+
+    // 4. vertex CSR: stable sort of (v, j) by v; keys land in `key`, values in vadj
+    if ((st = dalloc(&h->vadj, kappa, s, "vadj")) != HM_OK ||
+        (st = dalloc(&h->voff, (uint64_t)n + 1, s, "voff")) != HM_OK)
+        return st;
+    const int vbits = bit_width(n > 0 ? (uint64_t)(n - 1) : 0);
+    ce = radix_sort_pairs((const uint32_t *)h->pinsj, val, key, (uint32_t *)h->vadj, tk, tv, kappa,
+                          vbits, rscratch, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "vertex sort");
+    k_voff<<<grid_for(kappa + 1, kT, h->sm_count, 16), kT, 0, s>>>(key, (const uint32_t *)h->vadj,
+                                                                  kappa, n, h->voff, derr);
+    cudaEventRecord(ev.e[4], s);
+    cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
+    ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "vertex CSR");
+    if (herr.flags & kErrDup) {
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "duplicate pin: a vertex appears twice in one edge (vertex-sorted position %llu)",
+                 herr.first[3]);
+        set_error(buf);
+        return HM_EINVAL;
+    }
+    float ms = 0;
+    for (int i = 0; i < 4; ++i) {
+        cudaEventElapsedTime(&ms, ev.e[i], ev.e[i + 1]);
+        h->create_ms[i] = ms;
+    }
+    cudaEventElapsedTime(&ms, ev.e[0], ev.e[4]);
+    h->create_ms[4] = ms;
+
+    // weights in input numbering, for the result weight
+    if (h->weighted) {
+        if ((st = dalloc(&h->weights, (uint64_t)m, s, "weights")) != HM_OK) return st;
+        ce = cudaMemcpyAsync(h->weights, weights, (size_t)m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "weights copy");
+    }
+    return HM_OK;
+}
+
+}  // namespace hm

@@ -1,0 +1,170 @@
+// hm_internal.cuh - declarations shared by the translation units of libhm.
+//
+// Data layout in HBM (one handle; edges relabelled by decreasing priority,
+// j = 0 is the highest-priority edge):
+//   order  int32[m]     j -> input edge id
+//   eoffj  int64[m+1]   edge CSR in j order (E_id of Sec. 4.1)
+//   pinsj  int32[kappa] pins in j order (E_p)
+//   voff   int64[n+1]   vertex CSR offsets (V_id)
+//   vadj   int32[kappa] incident edges of every vertex, ascending j, i.e.
+//                       decreasing priority (V_p)
+//   alive  uint8[m]     1 = live edge (soft delete, Sec. 3.1)
+//   P      uint32[m]    pins of e that have not chosen e yet; e wins when it
+//                       reaches 0 (the P counter of Alg. 1 / Sec. 4.1, counted down)
+//   cur    int64[n]     T[v] as a cursor into vadj (Alg. 3), or kCurMatched /
+//                       kCurNone
+//   list0/list1 int32[n] active vertex lists (ping-pong)
+//   win    int32[min(m,n)] winners of the current round
+//   items  KillItem[n + kappa/kKillChunk + 1] kill ranges of the current round
+//   inM    uint8[m]     result mask, input numbering
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "hm.h"
+
+namespace hm {
+
+constexpr int64_t kCurMatched = -1;  // vertex covered by the matching
+constexpr int64_t kCurNone = -2;     // vertex has no live edge (or degree 0)
+constexpr int kKillChunk = 2048;     // max adjacency entries per kill item
+constexpr int kStatRounds = 4096;    // per-round counters kept for this many rounds
+
+// Device-resident loop state (one per handle).
+struct DevState {
+    int32_t round;        // current round, 1-based
+    int32_t parity;       // list index read by the current round
+    uint32_t cnt[2];      // sizes of list0 / list1
+    uint32_t nwin;        // winners appended this round
+    uint32_t nitems;      // kill items appended this round
+    int32_t status;       // HM_OK, HM_ETIMEOUT, HM_EINVAL (inconsistent input)
+    int32_t rounds_done;  // rounds that started with a live edge
+    int32_t finished;     // 1 once the loop has stopped
+    int32_t fault;        // nonzero: an internal consistency check failed
+    unsigned long long adv;        // counters of the current round
+    unsigned long long kills;
+    unsigned long long winpins;
+    unsigned long long proposals;
+};
+
+struct KillItem {
+    int64_t begin;
+    int64_t end;
+};
+
+// Everything a round kernel touches; passed by value.
+struct RoundArgs {
+    DevState *st;
+    const int64_t *voff;
+    const int32_t *vadj;
+    const int64_t *eoffj;
+    const int32_t *pinsj;
+    const int32_t *order;
+    uint8_t *alive;
+    uint32_t *P;
+    int64_t *cur;
+    int32_t *list0;
+    int32_t *list1;
+    int32_t *win;
+    KillItem *items;
+    uint8_t *inM;
+    int64_t *stats;        // [kStatRounds][HM_STATS_COLS]
+    int64_t n;
+    int64_t m;
+    int64_t cap;           // round cap
+    uint64_t item_cap;     // capacity of items
+    uint64_t win_cap;      // capacity of win
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
+
+struct Handle {
+    int device = 0;
+    int64_t n = 0, m = 0;
+    uint64_t kappa = 0;
+    bool weighted = true;
+    uint64_t seed = 0;
+    int sm_count = 0;
+    // device buffers (owned)
+    int64_t *voff = nullptr;
+    int32_t *vadj = nullptr;
+    int64_t *eoffj = nullptr;
+    int32_t *pinsj = nullptr;
+    int32_t *order = nullptr;
+    float *weights = nullptr;   // input numbering, for the result weight
+    uint8_t *alive = nullptr;
+    uint32_t *P = nullptr;
+    int64_t *cur = nullptr;
+    int32_t *list0 = nullptr, *list1 = nullptr;
+    int32_t *win = nullptr;
+    KillItem *items = nullptr;
+    uint8_t *inM = nullptr;
+    int64_t *stats = nullptr;
+    DevState *st = nullptr;
+    // result scratch
+    int32_t *res_idx = nullptr;
+    float *res_w = nullptr;
+    uint32_t *res_part = nullptr;
+    uint64_t item_cap = 0, win_cap = 0;
+    int64_t cap = 0;
+    // graph
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int64_t graph_cap = -1;
+    cudaEvent_t done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool matched_once = false;
+    double create_ms[5] = {0, 0, 0, 0, 0};
+    // pinned host staging
+    DevState *h_st = nullptr;
+};
+
+// ---- error reporting (api.cu) ----
+void set_error(const std::string &msg);
+hm_status cuda_fail(cudaError_t e, const char *what);
+
+// ---- primitives (prims.cu) ----
+// Exclusive scan of n values; out may alias in. If total != nullptr the sum
+// of all n values is written there. scratch must hold scan_scratch_elems(n).
+size_t scan_scratch_elems(uint64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *total,
+                               uint32_t *scratch, cudaStream_t s);
+cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, uint64_t n, int64_t *total,
+                               int64_t *scratch, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs by key bits [0, end_bit).
+// Inputs are not modified. tmp_k/tmp_v: n elements each. scratch: radix_scratch_elems(n).
+size_t radix_scratch_elems(uint64_t n);
+cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in,
+                             uint32_t *keys_out, uint32_t *vals_out,
+                             uint32_t *tmp_k, uint32_t *tmp_v, uint64_t n, int end_bit,
+                             uint32_t *scratch, cudaStream_t s);
+// Stable compaction of the indices i with flags[i] != 0 into idx_out (and
+// w[i] into w_out when w != nullptr). part: compact_scratch_elems(n) + 1;
+// the count is left in part[compact_scratch_elems(n)].
+size_t compact_scratch_elems(uint64_t n);
+cudaError_t compact_flags(const uint8_t *flags, uint64_t n, const float *w, int32_t *idx_out,
+                          float *w_out, uint32_t *part, cudaStream_t s);
+
+// ---- create (create.cu) ----
+hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
+                            const float *weights, cudaStream_t s);
+
+// ---- rounds (rounds.cu) ----
+RoundArgs round_args(const Handle *h);
+hm_status alloc_round_state(Handle *h, cudaStream_t s);
+hm_status launch_match_graph(Handle *h, cudaStream_t s);
+hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches);
+cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);
+void free_handle_buffers(Handle *h);
+
+inline unsigned grid_for(uint64_t work, int threads, int sm_count, int per_sm) {
+    uint64_t need = (work + threads - 1) / threads;
+    uint64_t cap = (uint64_t)sm_count * per_sm;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+}  // namespace hm

@@ -1,0 +1,256 @@
+"""GPU path vs the CPU oracle, through the C ABI (libhm.so).
+
+The order on edges is strict, so the matching is unique: the matched edge
+set, the round count, the per-round winner counts and the matching weight
+(float64 sum in ascending id order on both sides) must be identical. The
+per-vertex state after a capped run (T[v] of round r, or matched) must
+equal the oracle's state after r rounds.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2602_22976_gb300 as hmlib
+from conftest import golden_cases, golden_hypergraph
+
+pytestmark = pytest.mark.gpu
+
+OK, EINVAL, ETIMEOUT = hmlib.HM_OK, hmlib.HM_EINVAL, hmlib.HM_ETIMEOUT
+WIN = hmlib.STAT_COLUMNS.index("winners")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    hmlib.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    hmlib.lib()
+
+
+def run_gpu(h, cap=None):
+    with hmlib.Matcher.from_hypergraph(h) as mt:
+        if cap is not None:
+            mt.set_round_cap(cap)
+        mt.match()
+        res = mt.result(allow=(OK, ETIMEOUT))
+        stats = mt.round_stats()
+        vs = mt.vertex_state()
+    return res, stats, vs
+
+
+def assert_parity(h, res=None, stats=None, o=None):
+    if res is None:
+        res, stats, _ = run_gpu(h)
+    o = o or oracle.match(h)
+    assert res.status == OK
+    assert res.rounds == o.rounds
+    assert np.array_equal(res.edges, o.edges)
+    assert res.count == int(o.in_matching.sum())
+    assert stats[:o.rounds, WIN].tolist() == o.round_stats[:, 2].tolist()
+    assert res.weight == oracle.weight(h, o.in_matching)
+    return o
+
+
+@pytest.mark.parametrize("case", golden_cases(), ids=lambda c: c["name"])
+def test_golden(case):
+    h = golden_hypergraph(case)
+    res, stats, _ = run_gpu(h)
+    assert res.edges.tolist() == case["matching"]
+    assert res.rounds == case["rounds"]
+    assert_parity(h, res, stats)
+
+
+def test_small_config():
+    """n=10,000, m=20,000, |e| ~ U{2..8}, weights in (0,1], seed 1."""
+    assert_parity(synth.small())
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_powerlaw_scaled(seed):
+    """Power-law shape (Zipf(2) sizes on [2,1024], gamma=2.2 degrees) at 1/10 scale."""
+    assert_parity(synth.large(seed=seed, n=1_000_000, m=2_000_000))
+
+
+def test_unweighted_scaled():
+    assert_parity(synth.unweighted(seed=1, n=400_000, m=800_000))
+    assert_parity(synth.unweighted(seed=7, n=10_000, m=20_000))
+
+
+def test_ties_everywhere():
+    """Only two weight values: the id tie-break decides most argmaxes."""
+    h = synth.small(seed=4, n=3000, m=12_000)
+    h.weights = np.where(h.weights > 0.5, 1.0, 0.5).astype(np.float32)
+    assert_parity(h)
+
+
+def test_degenerate_inputs():
+    assert_parity(synth.from_edges(5, [], []))                      # no edges
+    assert_parity(synth.from_edges(1, [[0]], [1.0]))                # one vertex, one edge
+    assert_parity(synth.from_edges(100, [[3], [3], [7]], [0.5, 0.5, 0.25]))  # size-1 edges, tie
+    assert_parity(synth.from_edges(50, [[0, 49]], [2.0]))           # mostly isolated vertices
+
+
+def test_big_edges_and_hubs():
+    """Edge sizes across 32/256/2048/4096 and a hub whose kill range is
+    split into several chunks."""
+    rng = np.random.default_rng(0)
+    n = 20_000
+    edges, w = [], []
+    for k in (31, 32, 33, 255, 256, 257, 2047, 2048, 2049, 4095, 4096, 5000):
+        edges.append(sorted(rng.choice(n, size=k, replace=False).tolist()))
+        w.append(float(rng.integers(1, 1 << 24)) / (1 << 24))
+    for i in range(9000):  # hub: vertex 0 in 9000 small edges
+        e = [0] + rng.choice(np.arange(1, n), size=int(rng.integers(1, 4)), replace=False).tolist()
+        edges.append(sorted(e))
+        w.append(float(rng.integers(1, 1 << 24)) / (1 << 24))
+    for i in range(20_000):
+        edges.append(sorted(rng.choice(n, size=int(rng.integers(2, 6)), replace=False).tolist()))
+        w.append(float(rng.integers(1, 1 << 24)) / (1 << 24))
+    h = synth.from_edges(n, edges, w)
+    assert_parity(h)
+    # make the hub's best edge the global best so it is matched in round 1
+    w2 = list(w)
+    w2[12] = 1.0
+    assert_parity(synth.from_edges(n, edges, w2))
+
+
+def test_long_path_many_rounds():
+    m = 3001
+    h = synth.from_edges(m + 1, [[i, i + 1] for i in range(m)], [(i + 1) / 4096 for i in range(m)])
+    o = assert_parity(h)
+    assert o.rounds == math.ceil(m / 2)
+
+
+@pytest.mark.parametrize("cap", [1, 2, 3])
+def test_vertex_state_after_capped_rounds(cap):
+    """a1 parity: T[v] after round r equals the oracle's argmax of round r."""
+    for h in (synth.small(seed=5, n=5000, m=15_000), synth.large(seed=6, n=100_000, m=200_000)):
+        res, stats, vs = run_gpu(h, cap=cap)
+        o = oracle.match(h, max_rounds=cap)
+        assert res.status == ETIMEOUT
+        assert res.rounds == cap
+        assert np.array_equal(vs, oracle.vertex_state(o))
+        assert np.array_equal(res.edges, o.edges)
+
+
+def test_round_cap_timeout_on_path():
+    h = synth.from_edges(10, [[i, i + 1] for i in range(9)], [(i + 1) / 16 for i in range(9)])
+    res, _, _ = run_gpu(h, cap=1)
+    assert res.status == ETIMEOUT and res.rounds == 1 and res.edges.tolist() == [8]
+    with hmlib.Matcher.from_hypergraph(h) as mt:
+        mt.set_round_cap(1)
+        mt.match()
+        with pytest.raises(hmlib.HMError) as ei:
+            mt.result()
+        assert ei.value.status == ETIMEOUT
+
+
+def test_repeat_profile_and_device_result():
+    h = synth.large(seed=2, n=200_000, m=400_000)
+    o = oracle.match(h)
+    with hmlib.Matcher.from_hypergraph(h) as mt:
+        for _ in range(3):
+            mt.match()
+            res = mt.result()
+            assert np.array_equal(res.edges, o.edges) and res.rounds == o.rounds
+        prof = mt.profile()
+        res = mt.result()
+        assert np.array_equal(res.edges, o.edges) and res.rounds == o.rounds
+        assert prof["argmax"][1] == prof["kill"][1] >= o.rounds
+        mask = torch.zeros(h.m, dtype=torch.uint8, device="cuda")
+        mt.result_device(mask)
+        torch.cuda.synchronize()
+        assert np.array_equal(mask.cpu().numpy(), o.in_matching)
+        s = torch.cuda.Stream()
+        mt.match(stream=s)
+        res = mt.result()
+        assert np.array_equal(res.edges, o.edges)
+
+
+def test_solve_host_matches_handle_path():
+    h = synth.small(seed=8)
+    o = oracle.match(h)
+    res = hmlib.solve_host(h)
+    assert np.array_equal(res.edges, o.edges) and res.rounds == o.rounds
+    assert res.weight == oracle.weight(h, o.in_matching)
+    hu = synth.unweighted(seed=3, n=10_000, m=20_000)
+    ou = oracle.match(hu)
+    ru = hmlib.solve_host(hu)
+    assert np.array_equal(ru.edges, ou.edges) and ru.rounds == ou.rounds
+
+
+# ------------------------------------------------------------------ errors
+
+def _create(n, m, eoff, pins, w, flags=0):
+    L = hmlib.lib()
+    h = ctypes.c_void_p()
+    st = L.hm_create(ctypes.byref(h), n, m, eoff, pins, w, 1, flags, None)
+    if st == OK:
+        L.hm_destroy(h)
+    return st, hmlib.last_error()
+
+
+def _dev(a, dt):
+    return torch.tensor(a, dtype=dt, device="cuda")
+
+
+def test_invalid_inputs_rejected():
+    i64, i32, f32 = torch.int64, torch.int32, torch.float32
+    eoff = _dev([0, 2, 4], i64)
+    pins = _dev([0, 1, 1, 2], i32)
+    w = _dev([0.5, 0.25], f32)
+    assert _create(3, 2, eoff.data_ptr(), pins.data_ptr(), w.data_ptr())[0] == OK
+    cases = {
+        "eoff[0]": (_dev([1, 2, 4], i64), pins, w, 0),
+        "empty edge": (_dev([0, 2, 2, 4], i64), _dev([0, 1, 1, 2], i32), _dev([0.5, 0.5, 0.5], f32), 0),
+        "decreasing": (_dev([0, 3, 2, 4], i64), _dev([0, 1, 2, 2], i32), _dev([0.5, 0.5, 0.5], f32), 0),
+        "pin >= n": (eoff, _dev([0, 1, 1, 3], i32), w, 0),
+        "pin < 0": (eoff, _dev([0, -1, 1, 2], i32), w, 0),
+        "zero weight": (eoff, pins, _dev([0.0, 0.5], f32), 0),
+        "-0.0 weight": (eoff, pins, _dev([-0.0, 0.5], f32), 0),
+        "negative weight": (eoff, pins, _dev([0.5, -1.0], f32), 0),
+        "inf weight": (eoff, pins, _dev([float("inf"), 0.5], f32), 0),
+        "nan weight": (eoff, pins, _dev([float("nan"), 0.5], f32), 0),
+        "duplicate pin": (eoff, _dev([0, 0, 1, 2], i32), w, 0),
+    }
+    for name, (e, p, ww, fl) in cases.items():
+        m = e.numel() - 1
+        st, msg = _create(3, m, e.data_ptr(), p.data_ptr(), ww.data_ptr(), fl)
+        assert st == EINVAL, (name, st, msg)
+        assert msg, name
+    # unweighted ignores (invalid) weights
+    assert _create(3, 2, eoff.data_ptr(), pins.data_ptr(), _dev([0.0, -1.0], f32).data_ptr(),
+                   hmlib.HM_UNWEIGHTED)[0] == OK
+    # NULL weights without HM_UNWEIGHTED; host memory instead of device memory
+    assert _create(3, 2, eoff.data_ptr(), pins.data_ptr(), None)[0] == EINVAL
+    host = np.array([0, 2, 4], dtype=np.int64)
+    st, msg = _create(3, 2, host.ctypes.data, pins.data_ptr(), w.data_ptr())
+    assert st == EINVAL and "device memory" in msg
+    torch.cuda.synchronize()
+
+
+def test_no_match_yet_and_null_handle():
+    h = synth.small(seed=1, n=100, m=200)
+    with hmlib.Matcher.from_hypergraph(h) as mt:
+        with pytest.raises(hmlib.HMError):
+            mt.result()
+    assert hmlib.lib().hm_match(None, None) == EINVAL
+
+
+# ------------------------------------------------------------------ full size
+
+@pytest.mark.slow
+def test_full_size_powerlaw():
+    """n=10M, m=20M, Zipf(2) sizes on [2,1024], gamma=2.2 degrees (kappa ~ 2.02e8)."""
+    h = synth.large()
+    assert_parity(h)
+
+
+@pytest.mark.slow
+def test_full_size_unweighted():
+    """n=4M, m=8M, |e| ~ U{2..8}, seeded hash priority."""
+    assert_parity(synth.unweighted())
