@@ -204,6 +204,40 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
                         int32_t *edges_out, int64_t *count_out, int32_t *rounds_out,
                         double *weight_out, void *cuda_stream);
 
+/*
+ * hm_match_noalloc - match one small hypergraph with one kernel launch and
+ * no memory allocation at all. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they
+ * need a matching - for example code that is capturing a CUDA graph on its
+ * stream (cudaMalloc would break the capture), a framework that hands out
+ * all device memory from its own arena, or a latency-bound loop that cannot
+ * afford cudaMalloc's synchronisation. The caller passes inputs and outputs;
+ * the working memory is a fixed 8 MiB array declared once in the library
+ * (every GPU that loads libhm.so reserves it until the process exits).
+ *
+ *   n, m, eoff, pins, weights, seed, flags   as hm_create (DEVICE memory)
+ *   in_matching  DEVICE uint8[m]: 1 = edge in M (same matching as hm_match)
+ *   result       DEVICE int32[2]: [0] = rounds, [1] = hm_status of the run
+ *                (HM_OK, or HM_EINVAL for an invalid edge range, pin or
+ *                weight; a vertex repeated inside an edge is not rejected
+ *                here and counts once)
+ *   cuda_stream  the launch is enqueued there; the call does not wait
+ *
+ * Limit: 9*n + m bytes (each part rounded up to 256) must fit in 8 MiB,
+ * e.g. n = 500,000 and m = 3,000,000. Larger inputs return HM_EINVAL with a
+ * message naming the size; use hm_create/hm_match for them.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. All calls share the one array and every call
+ * clears the parts it uses, so calls whose kernels overlap on the GPU
+ * (different streams, or several host threads) race and corrupt each other;
+ * serialise them. Errors returned directly: HM_EINVAL (sizes, flags, NULL or
+ * host pointers), HM_ECUDA (symbol lookup or launch failure).
+ */
+hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
+                           const float *weights, uint64_t seed, uint32_t flags,
+                           uint8_t *in_matching, int32_t *result, void *cuda_stream);
+
 /* hm_last_error - message of the last failure on this thread ("" if none). */
 const char *hm_last_error(void);
 

@@ -32,7 +32,7 @@ KERNELS = ("init", "argmax", "win", "kill", "round_end")
 # Every entry point of include/hm.h, in declaration order.
 ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_result", "hm_result_device",
                 "hm_round_stats", "hm_vertex_state", "hm_profile_match", "hm_create_ms",
-                "hm_solve_host", "hm_last_error", "hm_destroy")
+                "hm_solve_host", "hm_match_noalloc", "hm_last_error", "hm_destroy")
 
 LIB_PATH = _build.LIB
 _lib = None
@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
             "hm_profile_match": ([p, p, p, p], i32),
             "hm_create_ms": ([p, p], i32),
             "hm_solve_host": ([i64, i64, p, p, p, u64, u32, p, p, p, p, p], i32),
+            "hm_match_noalloc": ([i64, i64, p, p, p, u64, u32, p, p, p], i32),
             "hm_last_error": ([], ctypes.c_char_p),
             "hm_destroy": ([p], None),
         }
