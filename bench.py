@@ -242,12 +242,15 @@ def run_ours(args, world, rank, local):
     create_ms = mt.create_ms()
     kb = kernel_bytes(stats, h.n, h.m)
     dom = max(("argmax", "win", "kill"), key=lambda k: prof[k][0])
+    assert all(isinstance(prof[k], tuple) for k in hm.KERNELS)
     peaks = measured_peaks()
     achieved = kb[dom] / (prof[dom][0] / 1e3) / 1e9
     per_kernel = {k: {"ms": prof[k][0], "launches": prof[k][1], "alg_bytes": kb[k],
                       "gbs": (kb[k] / (prof[k][0] / 1e3) / 1e9) if prof[k][0] > 0 else None}
-                  for k in prof}
+                  for k in hm.KERNELS}
+    round_ms = [[round(float(x), 4) for x in row[:3]] for row in prof["rounds_ms"]]
     total_bytes = sum(kb.values())
+    loop_ms = sum(prof[k][0] for k in hm.KERNELS)
     rounds_run = int(prof["argmax"][1])
     launches = 1 + 4 * rounds_run
 
@@ -302,8 +305,10 @@ def run_ours(args, world, rank, local):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                          "peak_source": peaks["source"],
-                         "loop_gbs": total_bytes / (sum(v[0] for v in prof.values()) / 1e3) / 1e9},
+                         "loop_gbs": total_bytes / (loop_ms / 1e3) / 1e9},
             "kernels": per_kernel,
+            "round_ms_argmax_win_kill": round_ms,
+            "round_stats": stats.tolist(),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

@@ -174,6 +174,9 @@ hm_status hm_vertex_state(hm_handle *h, int32_t *best_edge_out);
  * `cuda_stream`, and report per kernel kind k (HM_K_*):
  *   ms_out[k]        summed device time of its launches (CUDA events)
  *   launches_out[k]  number of launches
+ *   round_ms_out     HOST double[max_rounds][4] or NULL: per round r the
+ *                    times of the argmax, win, kill and round-end launches
+ *   max_rounds       rows available in round_ms_out (0 if NULL)
  * The result equals hm_match's. Waits for completion. Used to measure each
  * kernel; hm_match is the production path. Errors: as hm_match.
  */
@@ -183,7 +186,8 @@ hm_status hm_vertex_state(hm_handle *h, int32_t *best_edge_out);
 #define HM_K_KILL    3  /* a3: deactivate edges of newly matched vertices */
 #define HM_K_ROUND   4  /* a4: round bookkeeping, termination test */
 #define HM_K_COUNT   5
-hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int64_t *launches_out);
+hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int64_t *launches_out,
+                           double *round_ms_out, int32_t max_rounds);
 
 /*
  * hm_create_ms - device time of the hm_create phases of this handle

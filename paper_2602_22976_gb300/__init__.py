@@ -68,7 +68,7 @@ def lib() -> ctypes.CDLL:
             "hm_result_device": ([p, p, p], i32),
             "hm_round_stats": ([p, p, i32, p], i32),
             "hm_vertex_state": ([p, p], i32),
-            "hm_profile_match": ([p, p, p, p], i32),
+            "hm_profile_match": ([p, p, p, p, p, i32], i32),
             "hm_create_ms": ([p, p], i32),
             "hm_solve_host": ([i64, i64, p, p, p, u64, u32, p, p, p, p, p], i32),
             "hm_match_noalloc": ([i64, i64, p, p, p, u64, u32, p, p, p], i32),
@@ -189,9 +189,12 @@ class Matcher:
     def profile(self, stream=None) -> dict:
         ms = np.zeros(len(KERNELS), dtype=np.float64)
         launches = np.zeros(len(KERNELS), dtype=np.int64)
+        rounds = np.zeros((4096, 4), dtype=np.float64)
         _check(lib().hm_profile_match(self.handle, _stream_handle(stream), ms.ctypes.data,
-                                      launches.ctypes.data))
-        return {k: (float(ms[i]), int(launches[i])) for i, k in enumerate(KERNELS)}
+                                      launches.ctypes.data, rounds.ctypes.data, 4096))
+        out = {k: (float(ms[i]), int(launches[i])) for i, k in enumerate(KERNELS)}
+        out["rounds_ms"] = rounds[:min(int(launches[1]), 4096)].copy()
+        return out
 
     def create_ms(self) -> dict:
         ms = np.zeros(5, dtype=np.float64)

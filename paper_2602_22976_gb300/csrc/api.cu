@@ -197,7 +197,8 @@ hm_status hm_match(hm_handle *hh, void *cuda_stream) {
     return HM_OK;
 }
 
-hm_status hm_profile_match(hm_handle *hh, void *cuda_stream, double *ms_out, int64_t *launches_out) {
+hm_status hm_profile_match(hm_handle *hh, void *cuda_stream, double *ms_out, int64_t *launches_out,
+                           double *round_ms_out, int32_t max_rounds) {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h) return einval("handle is NULL");
     if (!ms_out || !launches_out) return einval("output pointer is NULL");
@@ -208,7 +209,9 @@ hm_status hm_profile_match(hm_handle *hh, void *cuda_stream, double *ms_out, int
         g_err = "a match of this handle is still running on another stream";
         return HM_EBUSY;
     }
-    st = profile_match(h, s, ms_out, launches_out);
+    if (!round_ms_out) max_rounds = 0;
+    if (max_rounds < 0) return einval("max_rounds < 0");
+    st = profile_match(h, s, ms_out, launches_out, round_ms_out, max_rounds);
     h->last_stream = s;
     h->matched_once = true;
     return st;

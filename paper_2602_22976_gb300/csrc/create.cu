@@ -116,14 +116,19 @@ __global__ void k_relabel(const int64_t *__restrict__ eoff, const int32_t *__res
 
 // voff from the vertex-sorted pin list: position i starts the segments of
 // the vertices (sv[i-1], sv[i]] (degree-0 vertices get empty segments).
-// Also flags a vertex repeated inside one edge (equal (v, j) neighbours).
+// firstj[v] = the first entry of v's list (or -2 for degree 0). Also flags a
+// vertex repeated inside one edge (equal (v, j) neighbours).
 __global__ void k_voff(const uint32_t *__restrict__ sv, const uint32_t *__restrict__ vadj,
-                       uint64_t kappa, int64_t n, int64_t *__restrict__ voff, CreateErr *err) {
+                       uint64_t kappa, int64_t n, int64_t *__restrict__ voff,
+                       int32_t *__restrict__ firstj, CreateErr *err) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= kappa;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const int64_t lo = i == 0 ? 0 : (int64_t)sv[i - 1] + 1;
         const int64_t hi = i == kappa ? n : (int64_t)sv[i];
-        for (int64_t v = lo; v <= hi; ++v) voff[v] = (int64_t)i;
+        for (int64_t v = lo; v <= hi; ++v) {
+            voff[v] = (int64_t)i;
+            if (v < n) firstj[v] = (v == hi && i < kappa) ? (int32_t)vadj[i] : -2;
+        }
         if (i > 0 && i < kappa && sv[i] == sv[i - 1] && vadj[i] == vadj[i - 1])
             report(err, kErrDup, 3, i);
     }
@@ -276,14 +281,15 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
 
     // 4. vertex CSR: stable sort of (v, j) by v; keys land in `key`, values in vadj
     if ((st = dalloc(&h->vadj, kappa, s, "vadj")) != HM_OK ||
-        (st = dalloc(&h->voff, (uint64_t)n + 1, s, "voff")) != HM_OK)
+        (st = dalloc(&h->voff, (uint64_t)n + 1, s, "voff")) != HM_OK ||
+        (st = dalloc(&h->firstj, (uint64_t)n, s, "first entries")) != HM_OK)
         return st;
     const int vbits = bit_width(n > 0 ? (uint64_t)(n - 1) : 0);
     ce = radix_sort_pairs((const uint32_t *)h->pinsj, val, key, (uint32_t *)h->vadj, tk, tv, kappa,
                           vbits, rscratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "vertex sort");
     k_voff<<<grid_for(kappa + 1, kT, h->sm_count, 16), kT, 0, s>>>(key, (const uint32_t *)h->vadj,
-                                                                  kappa, n, h->voff, derr);
+                                                                  kappa, n, h->voff, h->firstj, derr);
     cudaEventRecord(ev.e[4], s);
     cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
     ce = cudaStreamSynchronize(s);

@@ -11,10 +11,18 @@
 //   alive  uint8[m]     1 = live edge (soft delete, Sec. 3.1)
 //   P      uint32[m]    pins of e that have not chosen e yet; e wins when it
 //                       reaches 0 (the P counter of Alg. 1 / Sec. 4.1, counted down)
-//   cur    int64[n]     T[v] as a cursor into vadj (Alg. 3), or kCurMatched /
-//                       kCurNone
-//   list0/list1 int32[n] active vertex lists (ping-pong)
-//   win    int32[min(m,n)] winners of the current round
+//   vst    int2[n]      per-vertex state {T[v] as an edge j, cursor of T[v]
+//                       relative to voff[v]} (Alg. 3's T); T[v] = kCurMatched
+//                       once v is covered, kCurNone when v has no live edge
+//   firstj int32[n]     first entry of every vertex list (T[v] of round 1)
+//   list0/list1 int32[nregions*region] active vertex lists (ping-pong). The
+//                       list is cut into one region per warp of the argmax
+//                       grid; region g holds the active vertices of the
+//                       vertex range [g*region, (g+1)*region), compacted in
+//                       place, with its length in lcnt[parity][g]
+//   lcnt   uint32[2][nregions] region lengths
+//   wstage int32[nregions*region] per-region staging of a round's winners
+//   win    int32[min(m,n)] winners of the current round, contiguous
 //   items  KillItem[n + kappa/kKillChunk + 1] kill ranges of the current round
 //   inM    uint8[m]     result mask, input numbering
 #pragma once
@@ -28,9 +36,9 @@
 
 namespace hm {
 
-constexpr int64_t kCurMatched = -1;  // vertex covered by the matching
-constexpr int64_t kCurNone = -2;     // vertex has no live edge (or degree 0)
-constexpr int kKillChunk = 2048;     // max adjacency entries per kill item
+constexpr int32_t kCurMatched = -1;  // vertex covered by the matching
+constexpr int32_t kCurNone = -2;     // vertex has no live edge (or degree 0)
+constexpr int kKillChunk = 256;      // max adjacency entries per kill item
 constexpr int kStatRounds = 4096;    // per-round counters kept for this many rounds
 
 // Device-resident loop state (one per handle).
@@ -65,9 +73,14 @@ struct RoundArgs {
     const int32_t *order;
     uint8_t *alive;
     uint32_t *P;
-    int64_t *cur;
+    int2 *vst;
+    const int32_t *firstj;
     int32_t *list0;
     int32_t *list1;
+    uint32_t *lcnt;
+    int32_t *wstage;
+    uint32_t nregions;     // == warps of the k_argmax grid
+    uint32_t region;       // vertices per region (multiple of 32)
     int32_t *win;
     KillItem *items;
     uint8_t *inM;
@@ -97,8 +110,13 @@ struct Handle {
     float *weights = nullptr;   // input numbering, for the result weight
     uint8_t *alive = nullptr;
     uint32_t *P = nullptr;
-    int64_t *cur = nullptr;
+    int2 *vst = nullptr;
+    int32_t *firstj = nullptr;
     int32_t *list0 = nullptr, *list1 = nullptr;
+    uint32_t *lcnt = nullptr;
+    int32_t *wstage = nullptr;
+    uint32_t nregions = 0, region = 0;
+    unsigned argmax_grid = 0;
     int32_t *win = nullptr;
     KillItem *items = nullptr;
     uint8_t *inM = nullptr;
@@ -156,7 +174,8 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
 RoundArgs round_args(const Handle *h);
 hm_status alloc_round_state(Handle *h, cudaStream_t s);
 hm_status launch_match_graph(Handle *h, cudaStream_t s);
-hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches);
+hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches, double *round_ms,
+                        int32_t max_rounds);
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);
 void free_handle_buffers(Handle *h);
 

@@ -17,7 +17,8 @@
 //   k_round_end a4: counters, termination test, next active list, and the
 //               conditional of the CUDA graph's while node.
 // The active vertex list is compacted inside k_argmax (vertices that are
-// matched or have no live edge left drop out), warp-aggregated.
+// matched or have no live edge left drop out) with one block scan and one
+// counter atomic per 1024 list entries.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -27,7 +28,6 @@ namespace hm {
 namespace {
 
 constexpr int kT = 256;        // threads per block of the round kernels
-constexpr int kPerSM = 8;      // resident blocks per SM targeted by the grids
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -36,23 +36,69 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return r;
 }
 
-// Warp-aggregated append of `val` for the lanes with `pred`; all 32 lanes call.
 template <typename T>
-__device__ __forceinline__ void warp_append(bool pred, T val, T *out, uint32_t *counter) {
-    const unsigned mask = __ballot_sync(kFull, pred);
-    if (!mask) return;
+__device__ __forceinline__ T warp_inclusive_scan(T x) {
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
-    base = __shfl_sync(kFull, base, leader);
-    if (pred) out[base + __popc(mask & lanemask_lt())] = val;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan over a block of NT threads (one value each); *total gets
+// the block sum. s_warp: NT/32 + 1 words of shared memory. Ends with a
+// barrier, so s_warp may be reused right away.
+template <int NT = kT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t inc = warp_inclusive_scan(x);
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t t = lane < NT / 32 ? s_warp[lane] : 0u;
+        const uint32_t ti = warp_inclusive_scan(t);
+        if (lane < NT / 32) s_warp[lane] = ti - t;
+        if (lane == NT / 32 - 1) s_warp[NT / 32] = ti;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[wid] + inc - x;
+    *total = s_warp[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+// Largest i in [0, hi] with pre[i] <= k (pre ascending, pre[0] == 0 <= k).
+__device__ __forceinline__ int last_le(const uint32_t *pre, int hi, uint32_t k) {
+    int lo = 0;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
     return x;
+}
+
+// Sum over the block, added once per block to *dst.
+__device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned long long *s_red,
+                                              unsigned long long *dst) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_red[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kT / 32; ++w) t += s_red[w];
+        if (t) atomicAdd(dst, t);
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
@@ -63,7 +109,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
             a.P[i] = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
             a.inM[i] = 0;
         }
-        if (i < a.n) a.cur[i] = kCurNone;
+        if (i < a.n) a.vst[i] = make_int2(a.firstj[i], 0);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevState *st = a.st;
@@ -80,206 +126,303 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
     }
 }
 
-// a1: argmax (cursor advance) + proposals + list compaction.
-__global__ void __launch_bounds__(kT) k_argmax(RoundArgs a) {
+constexpr int kLaneSteps = 4;  // a lane walks at most 4 x 4 entries before its warp helps
+
+// First live entry of vadj[c, end) within kLaneSteps steps of four entries
+// (their loads are independent, so a step costs two dependent memory trips).
+// Returns its position (j = the edge), end if the list ran out, or -1 if
+// the budget ran out first.
+__device__ __forceinline__ int64_t next_live_bounded(const int32_t *__restrict__ vadj,
+                                                     const uint8_t *__restrict__ alive, int64_t c,
+                                                     int64_t end, int32_t &j) {
+#pragma unroll 1
+    for (int step = 0; step < kLaneSteps; ++step) {
+        if (c >= end) return end;
+        const int32_t e0 = __ldg(vadj + c);
+        const int32_t e1 = c + 1 < end ? __ldg(vadj + c + 1) : -1;
+        const int32_t e2 = c + 2 < end ? __ldg(vadj + c + 2) : -1;
+        const int32_t e3 = c + 3 < end ? __ldg(vadj + c + 3) : -1;
+        const bool a0 = __ldg(alive + e0) != 0;
+        const bool a1 = e1 >= 0 && __ldg(alive + e1) != 0;
+        const bool a2 = e2 >= 0 && __ldg(alive + e2) != 0;
+        const bool a3 = e3 >= 0 && __ldg(alive + e3) != 0;
+        if (a0) { j = e0; return c; }
+        if (a1) { j = e1; return c + 1; }
+        if (a2) { j = e2; return c + 2; }
+        if (a3) { j = e3; return c + 3; }
+        c += 4;
+    }
+    return c >= end ? end : -1;
+}
+
+// a1 for one vertex per lane: T[v] <- the first live entry of v's list at
+// or after its cursor. Returns whether v stays active; nb = the edge v newly
+// chose (it must count down P[nb]) or -1. All 32 lanes must call it: a lane
+// whose walk exceeds its budget is finished by the whole warp, 32 entries
+// per step (coalesced list read, one ballot).
+__device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok, int32_t v, int32_t &nb,
+                                              unsigned long long &adv) {
+    const int lane = threadIdx.x & 31;
+    const int32_t *__restrict__ vadj = a.vadj;
+    const uint8_t *__restrict__ alive = a.alive;
+    bool keep = false, walk = false, coop = false;
+    nb = -1;
+    int64_t vb = 0, from = 0, end = 0, cn = 0;
+    int32_t jj = 0;
+    if (ok) {
+        const int2 sv = a.vst[v];
+        if (sv.x >= 0) {
+            if (r == 1) {  // every edge is live in round 1: T[v] is the first entry
+                nb = sv.x;
+                keep = true;
+            } else if (__ldg(alive + sv.x)) {
+                keep = true;  // T[v] still live: unchanged
+            } else {
+                vb = __ldg(a.voff + v);
+                end = __ldg(a.voff + v + 1);
+                from = vb + sv.y;
+                walk = true;
+                cn = next_live_bounded(vadj, alive, from + 1, end, jj);
+                coop = cn < 0;
+            }
+        }
+    }
+    unsigned cm = __ballot_sync(kFull, coop);
+    while (cm) {
+        const int src = __ffs(cm) - 1;
+        int64_t p = __shfl_sync(kFull, from, src) + 1 + 4 * kLaneSteps;
+        const int64_t e = __shfl_sync(kFull, end, src);
+        int64_t fpos = e;
+        int32_t fj = 0;
+        while (p < e) {
+            const int64_t q = p + lane;
+            const int32_t ej = q < e ? __ldg(vadj + q) : -1;
+            const unsigned lm = __ballot_sync(kFull, ej >= 0 && __ldg(alive + ej) != 0);
+            if (lm) {
+                const int f = __ffs(lm) - 1;
+                fpos = p + f;
+                fj = __shfl_sync(kFull, ej, f);
+                break;
+            }
+            p += 32;
+        }
+        if (lane == src) {
+            cn = fpos;
+            jj = fj;
+        }
+        cm &= cm - 1;
+    }
+    if (walk) {
+        adv += (unsigned long long)(cn - from);
+        if (cn < end) {
+            a.vst[v] = make_int2(jj, (int32_t)(cn - vb));
+            nb = jj;
+            keep = true;
+        } else {
+            a.vst[v] = make_int2(kCurNone, 0);
+        }
+    }
+    return keep;
+}
+
+// a1: argmax (cursor advance) + proposals + win test + list compaction.
+// Warp g owns region g of the active list (the active vertices of one
+// vertex range) and compacts it in place into the other list with ballots:
+// no barrier and no shared counter inside the loop, so a lane that walks a
+// long run of dead entries only holds up its own warp. T[v] is kept as an
+// edge id, so the common case - T[v] still live - costs one state read and
+// one flag read. At the end each block reserves one slot range for its
+// warps' winners and copies them into the contiguous winner list.
+__global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
+    __shared__ unsigned long long s_red[kT / 32];
+    __shared__ uint32_t s_keep[kT / 32], s_won[kT / 32];
+    __shared__ uint32_t s_wbase;
     DevState *st = a.st;
     const int r = st->round;
     const int par = st->parity;
-    const uint64_t cnt = r == 1 ? (uint64_t)a.n : st->cnt[par];
     const int32_t *in = par ? a.list1 : a.list0;
     int32_t *out = par ? a.list0 : a.list1;
-    uint32_t *out_cnt = &st->cnt[par ^ 1];
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    const uint32_t *cnt_in = a.lcnt + (size_t)par * a.nregions;
+    uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const uint32_t g = blockIdx.x * (kT / 32) + wib;
     unsigned long long adv = 0, props = 0;
-    for (uint64_t base = warp * 32; base < cnt; base += nwarps * 32) {
-        const uint64_t idx = base + lane;
-        bool keep = false;
-        int32_t v = 0, nb = -1;
-        if (idx < cnt) {
-            if (r == 1) {
-                v = (int32_t)idx;
-                const int64_t c0 = a.voff[v], c1 = a.voff[v + 1];
-                if (c0 < c1) {  // every edge is live in round 1: T[v] = first entry
-                    a.cur[v] = c0;
-                    nb = a.vadj[c0];
-                    keep = true;
-                }
-            } else {
-                v = in[idx];
-                int64_t c = a.cur[v];
-                if (c >= 0) {
-                    int32_t j = a.vadj[c];
-                    if (a.alive[j]) {
-                        keep = true;  // T[v] still live: unchanged
-                    } else {
-                        const int64_t end = a.voff[v + 1];
-                        const int64_t c0 = c;
-                        for (++c; c < end; ++c) {
-                            j = a.vadj[c];
-                            if (a.alive[j]) break;
-                        }
-                        adv += (unsigned long long)(c - c0);
-                        if (c < end) {
-                            a.cur[v] = c;
-                            nb = j;
-                            keep = true;
-                        } else {
-                            a.cur[v] = kCurNone;
-                        }
-                    }
-                }
+    uint32_t kept = 0, won = 0;
+    if (g < a.nregions) {
+        const uint64_t base = (uint64_t)g * a.region;
+        uint32_t count;
+        if (r == 1) {
+            const int64_t left = a.n - (int64_t)base;
+            count = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.region ? left : (int64_t)a.region);
+        } else {
+            count = cnt_in[g];
+        }
+        for (uint32_t i0 = 0; i0 < count; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool ok = i < count;
+            const int32_t v = ok ? (r == 1 ? (int32_t)(base + i) : in[base + i]) : 0;
+            int32_t nb;
+            const bool keep = argmax_vertex(a, r, ok, v, nb, adv);
+            bool w = false;
+            if (nb >= 0) {
+                ++props;
+                w = atomicSub(&a.P[nb], 1u) == 1u;
             }
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (keep) out[base + kept + __popc(km & lt)] = v;
+            kept += __popc(km);
+            const unsigned wm = __ballot_sync(kFull, w);
+            if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
+            won += __popc(wm);
         }
-        bool won = false;
-        if (nb >= 0) {
-            ++props;
-            won = atomicSub(&a.P[nb], 1u) == 1u;
-        }
-        warp_append<int32_t>(keep, v, out, out_cnt);
-        warp_append<int32_t>(won, nb, a.win, &st->nwin);
+        if (lane == 0) cnt_out[g] = kept;
     }
-    adv = warp_sum_u64(adv);
-    props = warp_sum_u64(props);
     if (lane == 0) {
-        if (adv) atomicAdd(&st->adv, adv);
-        if (props) atomicAdd(&st->proposals, props);
+        s_keep[wib] = kept;
+        s_won[wib] = won;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tk = 0, tw = 0;
+        for (int w = 0; w < kT / 32; ++w) {
+            tk += s_keep[w];
+            const uint32_t t = s_won[w];
+            s_won[w] = tw;
+            tw += t;
+        }
+        if (tk) atomicAdd(&st->cnt[par ^ 1], tk);
+        s_wbase = tw ? atomicAdd(&st->nwin, tw) : 0u;
+    }
+    __syncthreads();
+    if (g < a.nregions)
+        for (uint32_t i = lane; i < won; i += 32)
+            a.win[s_wbase + s_won[wib] + i] = a.wstage[(uint64_t)g * a.region + i];
+    block_add_u64(adv, s_red, &st->adv);
+    block_add_u64(props, s_red, &st->proposals);
 }
 
-// a2: warp per winner. Marks e in M and every vertex of e as matched; each
-// vertex emits [cursor, end of its list) as kill ranges of <= kKillChunk.
+// a2: winners join M; every vertex of a winner is marked matched and emits
+// its list from the cursor on as kill items of <= kKillChunk entries.
+// Blocks take kT winners at a time and spread their pins evenly over the
+// threads (prefix sum of edge sizes + binary search); item slots are
+// reserved with one atomic per kT pins and written by the whole block.
 __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
+    __shared__ int64_t s_wbeg[kT];
+    __shared__ int32_t s_wj[kT];
+    __shared__ uint32_t s_wpre[kT + 1];
+    __shared__ int64_t s_c[kT], s_end[kT];
+    __shared__ uint32_t s_ipre[kT + 1];
+    __shared__ uint32_t s_warp[kT / 32 + 1];
+    __shared__ uint32_t s_ibase;
+    __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
     const uint32_t nw = st->nwin;
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    const int t = threadIdx.x;
     unsigned long long kills = 0, winpins = 0;
-    for (uint64_t w = warp; w < nw; w += nwarps) {
-        const int32_t j = a.win[w];
-        const int64_t b = a.eoffj[j], e = a.eoffj[j + 1];
-        if (lane == 0) {
+    for (uint64_t wb = (uint64_t)blockIdx.x * kT; wb < nw; wb += (uint64_t)gridDim.x * kT) {
+        uint32_t len = 0;
+        if (wb + t < nw) {
+            const int32_t j = a.win[wb + t];
+            const int64_t b = a.eoffj[j], e = a.eoffj[j + 1];
+            s_wbeg[t] = b;
+            s_wj[t] = j;
+            len = (uint32_t)(e - b);
             a.inM[a.order[j]] = 1;
-            winpins += (unsigned long long)(e - b);
+            winpins += len;
         }
-        for (int64_t i0 = b; i0 < e; i0 += 32) {
-            const int64_t i = i0 + lane;
-            int64_t c = 0, end = 0;
+        uint32_t npins;
+        s_wpre[t] = block_exclusive_scan(len, s_warp, &npins);
+        if (t == 0) s_wpre[kT] = npins;
+        __syncthreads();
+        for (uint32_t p0 = 0; p0 < npins; p0 += kT) {
+            const uint32_t q = p0 + t;
             uint32_t nch = 0;
-            if (i < e) {
-                const int32_t v = a.pinsj[i];
-                c = a.cur[v];
-                end = a.voff[v + 1];
-                // T[v] must point at e: it chose e, and nothing moves it
-                if (c >= a.voff[v] && c < end && a.vadj[c] == j) {
-                    a.cur[v] = kCurMatched;
+            int64_t c = 0, end = 0;
+            if (q < npins) {
+                const int w = last_le(s_wpre, kT - 1, q);
+                const int32_t v = __ldg(a.pinsj + s_wbeg[w] + (q - s_wpre[w]));
+                const int2 sv = a.vst[v];
+                c = __ldg(a.voff + v) + sv.y;
+                end = __ldg(a.voff + v + 1);
+                // T[v] must be the winner: v chose it, and nothing moves it
+                if (sv.x == s_wj[w] && c < end) {
+                    a.vst[v] = make_int2(kCurMatched, 0);
                     nch = (uint32_t)((end - c + kKillChunk - 1) / kKillChunk);
                     kills += (unsigned long long)(end - c);
                 } else {
                     st->fault = 1;
                 }
             }
-            // warp exclusive scan of the chunk counts -> item slots
-            uint32_t inc = nch;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, inc, d);
-                if (lane >= d) inc += y;
+            s_c[t] = c;
+            s_end[t] = end;
+            uint32_t nitems;
+            s_ipre[t] = block_exclusive_scan(nch, s_warp, &nitems);
+            if (t == 0) {
+                s_ipre[kT] = nitems;
+                uint32_t b = nitems ? atomicAdd(&st->nitems, nitems) : 0u;
+                if ((uint64_t)b + nitems > a.item_cap) {
+                    st->fault = 2;
+                    b = 0xFFFFFFFFu;
+                }
+                s_ibase = b;
             }
-            const uint32_t total = __shfl_sync(kFull, inc, 31);
-            uint32_t base = 0;
-            if (lane == 0 && total) base = atomicAdd(&st->nitems, total);
-            base = __shfl_sync(kFull, base, 0);
-            uint64_t slot = (uint64_t)base + inc - nch;
-            if (slot + nch > a.item_cap) {
-                if (nch) st->fault = 2;
-                nch = 0;
+            __syncthreads();
+            const uint32_t ib = s_ibase;
+            if (ib != 0xFFFFFFFFu) {
+                for (uint32_t x = t; x < nitems; x += kT) {
+                    const int pi = last_le(s_ipre, kT - 1, x);
+                    const int64_t lo = s_c[pi] + (int64_t)(x - s_ipre[pi]) * kKillChunk;
+                    const int64_t hi = lo + kKillChunk < s_end[pi] ? lo + kKillChunk : s_end[pi];
+                    a.items[(uint64_t)ib + x] = KillItem{lo, hi};
+                }
             }
-            for (uint32_t k = 0; k < nch; ++k) {
-                const int64_t lo = c + (int64_t)k * kKillChunk;
-                const int64_t hi = lo + kKillChunk < end ? lo + kKillChunk : end;
-                a.items[slot + k] = KillItem{lo, hi};
-            }
+            __syncthreads();
         }
     }
-    kills = warp_sum_u64(kills);
-    winpins = warp_sum_u64(winpins);
-    if (lane == 0) {
-        if (kills) atomicAdd(&st->kills, kills);
-        if (winpins) atomicAdd(&st->winpins, winpins);
-    }
+    block_add_u64(kills, s_red, &st->kills);
+    block_add_u64(winpins, s_red, &st->winpins);
 }
 
-// a3: deactivate every edge listed in a kill range. Blocks take batches of
-// kT ranges; the batch's entries are spread evenly over the block's threads
-// by a prefix sum of the range lengths and a binary search per entry.
+// a3: deactivate every entry of every kill item. A warp takes one item
+// (<= kKillChunk entries) at a time; each lane has four entries in flight.
 __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
-    __shared__ int64_t sbeg[kT];
-    __shared__ uint32_t spre[kT + 1];
-    __shared__ uint32_t warp_tot[kT / 32];
     DevState *st = a.st;
-    const uint32_t ni = min(st->nitems, (uint32_t)a.item_cap);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (uint64_t ib = (uint64_t)blockIdx.x * kT; ib < ni; ib += (uint64_t)gridDim.x * kT) {
-        uint32_t len = 0;
-        if (ib + threadIdx.x < ni) {
-            const KillItem it = a.items[ib + threadIdx.x];
-            sbeg[threadIdx.x] = it.begin;
-            len = (uint32_t)(it.end - it.begin);
+    const uint64_t ni = min((uint64_t)st->nitems, a.item_cap);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    const int32_t *__restrict__ vadj = a.vadj;
+    uint8_t *__restrict__ alive = a.alive;
+    for (uint64_t it = warp; it < ni; it += nwarps) {
+        const KillItem x = a.items[it];
+        for (int64_t p = x.begin + lane; p < x.end; p += 128) {
+            const int32_t j0 = __ldg(vadj + p);
+            const int32_t j1 = p + 32 < x.end ? __ldg(vadj + p + 32) : -1;
+            const int32_t j2 = p + 64 < x.end ? __ldg(vadj + p + 64) : -1;
+            const int32_t j3 = p + 96 < x.end ? __ldg(vadj + p + 96) : -1;
+            alive[j0] = 0;
+            if (j1 >= 0) alive[j1] = 0;
+            if (j2 >= 0) alive[j2] = 0;
+            if (j3 >= 0) alive[j3] = 0;
         }
-        uint32_t inc = len;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, inc, d);
-            if (lane >= d) inc += y;
-        }
-        if (lane == 31) warp_tot[wid] = inc;
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t t = lane < kT / 32 ? warp_tot[lane] : 0;
-            uint32_t ti = t;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, ti, d);
-                if (lane >= d) ti += y;
-            }
-            if (lane < kT / 32) warp_tot[lane] = ti - t;
-            if (lane == kT / 32 - 1) spre[kT] = ti;
-        }
-        __syncthreads();
-        spre[threadIdx.x] = warp_tot[wid] + inc - len;
-        __syncthreads();
-        const uint32_t total = spre[kT];
-        for (uint32_t k = threadIdx.x; k < total; k += kT) {
-            int lo = 0, hi = kT - 1;  // last item with spre[item] <= k
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (spre[mid] <= k) lo = mid; else hi = mid - 1;
-            }
-            const int64_t pos = sbeg[lo] + (int64_t)(k - spre[lo]);
-            a.alive[a.vadj[pos]] = 0;
-        }
-        __syncthreads();
     }
 }
 
-// a4: one thread. Records the round, decides whether another round runs.
-__global__ void k_round_end(RoundArgs a) {
-    if (threadIdx.x != 0) return;
-    DevState *st = a.st;
-    const int r = st->round, par = st->parity;
-    const uint32_t nw = st->nwin, next = st->cnt[par ^ 1];
+// Stats row of round r, termination test and next-round decision.
+// Returns 1 if another round must run.
+__device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t active, uint32_t nw,
+                            uint32_t next, unsigned long long adv, unsigned long long props,
+                            unsigned long long winpins, unsigned long long kills, uint32_t items) {
     if (r - 1 < kStatRounds) {
         int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
-        row[HM_STAT_ACTIVE] = r == 1 ? a.n : (int64_t)st->cnt[par];
-        row[HM_STAT_ADVANCE] = (int64_t)st->adv;
-        row[HM_STAT_PROPOSALS] = (int64_t)st->proposals;
+        row[HM_STAT_ACTIVE] = active;
+        row[HM_STAT_ADVANCE] = (int64_t)adv;
+        row[HM_STAT_PROPOSALS] = (int64_t)props;
         row[HM_STAT_WINNERS] = nw;
-        row[HM_STAT_WINPINS] = (int64_t)st->winpins;
-        row[HM_STAT_KILLS] = (int64_t)st->kills;
-        row[HM_STAT_ITEMS] = st->nitems;
+        row[HM_STAT_WINPINS] = (int64_t)winpins;
+        row[HM_STAT_KILLS] = (int64_t)kills;
+        row[HM_STAT_ITEMS] = items;
         row[HM_STAT_NEXT] = next;
     }
     int cont = 0;
@@ -298,6 +441,18 @@ __global__ void k_round_end(RoundArgs a) {
             else cont = 1;
         }
     }
+    return cont;
+}
+
+// a4: one thread. Records the round, decides whether another round runs.
+__global__ void k_round_end(RoundArgs a) {
+    if (threadIdx.x != 0) return;
+    DevState *st = a.st;
+    const int r = st->round, par = st->parity;
+    const uint32_t nw = st->nwin, next = st->cnt[par ^ 1];
+    const int64_t active = r == 1 ? a.n : (int64_t)st->cnt[par];
+    const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, st->kills,
+                            st->nitems);
     st->nwin = 0;
     st->nitems = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
@@ -311,25 +466,40 @@ __global__ void k_round_end(RoundArgs a) {
     if (a.use_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
 }
 
-__global__ void k_vertex_state(const int64_t *cur, const int32_t *vadj, const int32_t *order,
-                               int64_t n, int32_t *out) {
+__global__ void k_vertex_state(const int2 *vst, const int32_t *order, int64_t n, int32_t *out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = cur[v];
-        out[v] = c >= 0 ? order[vadj[c]] : (c == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
+        const int32_t j = vst[v].x;
+        out[v] = j >= 0 ? order[j] : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
     }
 }
 
-unsigned round_grid(const Handle *h) { return (unsigned)std::max(1, h->sm_count * kPerSM); }
+// Grid of a grid-stride round kernel: exactly the blocks that fit at once.
+template <typename K>
+unsigned resident_grid(const Handle *h, K kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kT, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 4;
+    }
+    return (unsigned)std::max(1, h->sm_count * per_sm);
+}
 
 void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
-    const unsigned g = round_grid(h);
+    static thread_local int cached_sms = -1;
+    static thread_local unsigned g_win = 0, g_kill = 0;
+    const unsigned g_arg = h->argmax_grid;
+    if (cached_sms != h->sm_count) {
+        g_win = resident_grid(h, k_win);
+        g_kill = resident_grid(h, k_kill);
+        cached_sms = h->sm_count;
+    }
     if (ev) cudaEventRecord(ev[0], s);
-    k_argmax<<<g, kT, 0, s>>>(a);
+    k_argmax<<<g_arg, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[1], s);
-    k_win<<<g, kT, 0, s>>>(a);
+    k_win<<<g_win, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
-    k_kill<<<g, kT, 0, s>>>(a);
+    k_kill<<<g_kill, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     k_round_end<<<1, 32, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[4], s);
@@ -425,9 +595,14 @@ RoundArgs round_args(const Handle *h) {
     a.order = h->order;
     a.alive = h->alive;
     a.P = h->P;
-    a.cur = h->cur;
+    a.vst = h->vst;
+    a.firstj = h->firstj;
     a.list0 = h->list0;
     a.list1 = h->list1;
+    a.lcnt = h->lcnt;
+    a.wstage = h->wstage;
+    a.nregions = h->nregions;
+    a.region = h->region;
     a.win = h->win;
     a.items = h->items;
     a.inM = h->inM;
@@ -448,9 +623,17 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     hm_status st;
     if ((st = dalloc(&h->alive, m, s, "alive")) != HM_OK) return st;
     if ((st = dalloc(&h->P, m, s, "P")) != HM_OK) return st;
-    if ((st = dalloc(&h->cur, n, s, "cursors")) != HM_OK) return st;
-    if ((st = dalloc(&h->list0, n, s, "active list")) != HM_OK) return st;
-    if ((st = dalloc(&h->list1, n, s, "active list")) != HM_OK) return st;
+    if ((st = dalloc(&h->vst, n, s, "vertex state")) != HM_OK) return st;
+    // one list region per warp of the argmax grid
+    h->argmax_grid = resident_grid(h, k_argmax);
+    h->nregions = h->argmax_grid * (kT / 32);
+    h->region = (uint32_t)((((n + h->nregions - 1) / h->nregions) + 31) / 32 * 32);
+    if (h->region == 0) h->region = 32;
+    const uint64_t lcap = (uint64_t)h->nregions * h->region;
+    if ((st = dalloc(&h->list0, lcap, s, "active list")) != HM_OK) return st;
+    if ((st = dalloc(&h->list1, lcap, s, "active list")) != HM_OK) return st;
+    if ((st = dalloc(&h->wstage, lcap, s, "winner staging")) != HM_OK) return st;
+    if ((st = dalloc(&h->lcnt, 2 * (uint64_t)h->nregions, s, "region lengths")) != HM_OK) return st;
     if ((st = dalloc(&h->win, h->win_cap, s, "winners")) != HM_OK) return st;
     if ((st = dalloc(&h->items, h->item_cap, s, "kill items")) != HM_OK) return st;
     if ((st = dalloc(&h->inM, m, s, "result mask")) != HM_OK) return st;
@@ -479,7 +662,8 @@ hm_status launch_match_graph(Handle *h, cudaStream_t s) {
     return HM_OK;
 }
 
-hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches) {
+hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches, double *round_ms,
+                        int32_t max_rounds) {
     for (int k = 0; k < HM_K_COUNT; ++k) {
         ms[k] = 0;
         launches[k] = 0;
@@ -503,7 +687,7 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
     cudaEventElapsedTime(&t, ev[5], ev[0]);
     ms[HM_K_INIT] += t;
     launches[HM_K_INIT] += 1;
-    for (;;) {
+    for (int32_t r = 0;; ++r) {
         launch_round(h, a, s, ev);
         cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
@@ -512,6 +696,7 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
             cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
             ms[HM_K_ARGMAX + k] += t;
             launches[HM_K_ARGMAX + k] += 1;
+            if (r < max_rounds) round_ms[(int64_t)r * 4 + k] = t;
         }
         if (h->h_st->finished) break;
     }
@@ -520,14 +705,14 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
 }
 
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
-    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(h->cur, h->vadj, h->order,
-                                                                                h->n, out_dev);
+    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(h->vst, h->order, h->n,
+                                                                                out_dev);
     return cudaGetLastError();
 }
 
 void free_handle_buffers(Handle *h) {
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
-                    h->cur, h->list0, h->list1, h->win, h->items, h->inM, h->stats, h->st,
+                    h->vst, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->win, h->items, h->inM, h->stats, h->st,
                     h->res_idx, h->res_w, h->res_part};
     for (void *p : bufs)
         if (p) cudaFree(p);
