@@ -122,20 +122,50 @@ class Clocks:
 
 
 def kernel_bytes(stats: np.ndarray, n: int, m: int) -> dict:
-    """Algorithmic bytes per kernel kind, summed over rounds (formulas in the design doc)."""
+    """Algorithmic bytes per kernel kind, summed over rounds (per-unit figures
+    in the design doc, section 6), from the per-round counters of hm_round_stats."""
     ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT = range(8)
-    b = {"init": float(m * (1 + 8 + 4 + 1) + n * 8), "argmax": 0.0, "win": 0.0, "kill": 0.0,
-         "round_end": 0.0}
+    b = {"init": float(m * (1 + 8 + 4 + 1) + n * (4 + 8)), "argmax": 0.0, "win": 0.0,
+         "kill": 0.0, "round_end": 0.0}
     for r, row in enumerate(stats):
         row = row.astype(np.float64)
-        if r == 0:
-            b["argmax"] += row[ACT] * 16 + row[PROP] * (8 + 4 + 8) + row[NEXT] * 4
-        else:
-            b["argmax"] += (row[ACT] * (4 + 8 + 4 + 1) + row[ADV] * (4 + 1)
-                            + row[PROP] * (8 + 8 + 8) + row[NEXT] * 4)
-        b["win"] += row[WIN] * (4 + 16 + 4 + 1) + row[WPIN] * (4 + 8 + 16 + 4 + 8) + row[ITEM] * 16
+        if r == 0:  # record read; proposal = P read+write; kept vertex = list write
+            b["argmax"] += row[ACT] * 16 + row[PROP] * 8 + row[NEXT] * 4
+        else:       # list + record + live flag; skipped entry = entry + flag;
+                    # proposal = record write + P read+write; kept vertex = list write
+            b["argmax"] += (row[ACT] * (4 + 16 + 1) + row[ADV] * (4 + 1)
+                            + row[PROP] * (8 + 8) + row[NEXT] * 4)
+        # winner: list, offset pair, order, mask; winner pin: pin, record read+write; item write
+        b["win"] += row[WIN] * (4 + 16 + 4 + 1) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 16
+        # item read; killed entry: entry + flag write
         b["kill"] += row[ITEM] * 16 + row[KILL] * (4 + 1)
     return b
+
+
+def kernel_source_hash() -> str:
+    """Hash of the round kernels' source: a stored ncu traffic figure is only
+    valid for the kernel version it was measured on."""
+    import hashlib
+    p = os.path.join(ROOT, "paper_2602_22976_gb300", "csrc", "rounds.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(kernel: str) -> float | None:
+    """Per-launch DRAM bytes of `kernel` at the full bench size, read from the
+    committed ncu summary (profiles/traffic.md) when it matches this source."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(p):
+        return None
+    want = kernel_source_hash()
+    for line in open(p):
+        parts = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == want:
+            try:
+                return float(parts[2])
+            except ValueError:
+                return None
+    return None
 
 
 def measured_peaks() -> dict:
@@ -250,9 +280,12 @@ def run_ours(args, world, rank, local):
                   for k in hm.KERNELS}
     round_ms = [[round(float(x), 4) for x in row[:3]] for row in prof["rounds_ms"]]
     total_bytes = sum(kb.values())
+    # random-access ceilings of this GPU for an array the size of the live flags
+    ra = hm.probe_random_access(max(h.m, 1 << 20), 200_000_000)
+    kills = float(stats[:, hm.STAT_COLUMNS.index("kills")].sum())
     loop_ms = sum(prof[k][0] for k in hm.KERNELS)
     rounds_run = int(prof["argmax"][1])
-    launches = 1 + 4 * rounds_run
+    launches = 1 + 4 * rounds_run  # init + four kernels per round
 
     out = {}
     if rank == 0:
@@ -303,9 +336,16 @@ def run_ours(args, world, rank, local):
                                     "p99": float(np.percentile(step_ms, 99))},
             "create_ms": create_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom),
+                         "alg_bytes_per_launch": kb[dom] / max(1, prof[dom][1]),
+                         "kernel_source": kernel_source_hash(),
                          "peak_source": peaks["source"],
                          "loop_gbs": total_bytes / (loop_ms / 1e3) / 1e9},
+            "random_access": {
+                "array_bytes": max(h.m, 1 << 20), "ceiling_gops": ra,
+                "kill_entries_gops": kills / (prof["kill"][0] / 1e3) / 1e9,
+                "note": "kill reads each target flag (rounds >= 2) and writes the live ones; "
+                        "its bound is the random 1-byte load/store rate, not HBM bandwidth"},
             "kernels": per_kernel,
             "round_ms_argmax_win_kill": round_ms,
             "round_stats": stats.tolist(),

@@ -197,6 +197,25 @@ hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int6
 hm_status hm_create_ms(hm_handle *h, double *ms_out);
 
 /*
+ * hm_probe_random_access - measure this GPU's rate of random single-element
+ * accesses (no counterpart in the paper). The round kernels gather and
+ * scatter 1-byte flags and 4-byte counters at random; their ceiling is this
+ * rate, not streaming bandwidth. Runs `ops` accesses of each kind at
+ * pseudo-random indices of a DEVICE scratch array of `array_bytes` bytes
+ * (allocated and freed here, stream-ordered on `cuda_stream`; 1 KiB .. 4 GiB)
+ * and writes the best of two timed runs, in 1e9 accesses per second, to
+ * HOST double[HM_PROBE_COUNT]. Waits for completion.
+ * Errors: HM_EINVAL, HM_ENOMEM, HM_ECUDA.
+ */
+#define HM_PROBE_STORE1  0  /* 1-byte store */
+#define HM_PROBE_LOAD1   1  /* 1-byte load (L2, bypassing L1) */
+#define HM_PROBE_LOAD4   2  /* 4-byte load (L2, bypassing L1) */
+#define HM_PROBE_RED4    3  /* 4-byte atomic subtract, result unused */
+#define HM_PROBE_ATOMIC4 4  /* 4-byte atomic subtract returning the old value */
+#define HM_PROBE_COUNT   5
+hm_status hm_probe_random_access(uint64_t array_bytes, uint64_t ops, double *gops_out, void *cuda_stream);
+
+/*
  * hm_solve_host - one call from HOST buffers to HOST result: copies eoff,
  * pins, weights (host memory; pinned memory gives full link bandwidth) to
  * the device on `cuda_stream`, runs hm_create + hm_match + hm_result and

@@ -32,7 +32,8 @@ KERNELS = ("init", "argmax", "win", "kill", "round_end")
 # Every entry point of include/hm.h, in declaration order.
 ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_result", "hm_result_device",
                 "hm_round_stats", "hm_vertex_state", "hm_profile_match", "hm_create_ms",
-                "hm_solve_host", "hm_match_noalloc", "hm_last_error", "hm_destroy")
+                "hm_probe_random_access", "hm_solve_host", "hm_match_noalloc", "hm_last_error",
+                "hm_destroy")
 
 LIB_PATH = _build.LIB
 _lib = None
@@ -70,6 +71,7 @@ def lib() -> ctypes.CDLL:
             "hm_vertex_state": ([p, p], i32),
             "hm_profile_match": ([p, p, p, p, p, i32], i32),
             "hm_create_ms": ([p, p], i32),
+            "hm_probe_random_access": ([u64, u64, p, p], i32),
             "hm_solve_host": ([i64, i64, p, p, p, u64, u32, p, p, p, p, p], i32),
             "hm_match_noalloc": ([i64, i64, p, p, p, u64, u32, p, p, p], i32),
             "hm_last_error": ([], ctypes.c_char_p),
@@ -217,6 +219,17 @@ class Matcher:
             self.close()
         except Exception:
             pass
+
+
+PROBES = ("store1B", "load1B", "load4B", "red4B", "atomic4B")
+
+
+def probe_random_access(array_bytes: int, ops: int = 200_000_000, stream=None) -> dict:
+    """Random single-element access rates of this GPU (1e9 per second)."""
+    out = np.zeros(len(PROBES), dtype=np.float64)
+    _check(lib().hm_probe_random_access(int(array_bytes), int(ops), out.ctypes.data,
+                                        _stream_handle(stream)))
+    return dict(zip(PROBES, out.tolist()))
 
 
 def solve_host(hg, stream=None, allow=(HM_OK,)) -> Result:

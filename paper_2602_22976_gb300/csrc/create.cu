@@ -96,21 +96,54 @@ __global__ void k_sizes_j(const int64_t *__restrict__ eoff, const uint32_t *__re
     }
 }
 
-// Warp per edge: pins of input edge order[j] -> pinsj at eoffj[j]; the
-// matching slots of jval receive j.
-__global__ void k_relabel(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
-                          const uint32_t *__restrict__ order, const int64_t *__restrict__ eoffj,
-                          int64_t m, int32_t *__restrict__ pinsj, uint32_t *__restrict__ jval) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < m; j += nwarps) {
-        const uint32_t e = order[j];
-        const int64_t src = eoff[e], dst = eoffj[j], len = eoffj[j + 1] - dst;
-        for (int64_t t = lane; t < len; t += 32) {
-            pinsj[dst + t] = pins[src + t];
-            jval[dst + t] = (uint32_t)j;
+// Pins of input edge order[j] -> pinsj[eoffj[j] ..]; the same slots of
+// jval receive j. Output-driven: a block fills kRelTile consecutive output
+// slots, loads the offsets of exactly the edges covering them (first[t] is
+// the edge containing the tile's first slot), locates each slot's edge by
+// binary search in shared memory, and writes both outputs coalesced
+// whatever the edge sizes.
+constexpr int kRelTile = 2048;
+
+// first[t] = the edge that contains output slot t*kRelTile.
+__global__ void k_tile_first(const int64_t *__restrict__ eoffj, int64_t m, uint64_t ntiles,
+                             int32_t *__restrict__ first) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = (uint64_t)eoffj[j], e = (uint64_t)eoffj[j + 1];
+        for (uint64_t t = (b + kRelTile - 1) / kRelTile; t * kRelTile < e && t < ntiles; ++t)
+            first[t] = (int32_t)j;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_relabel(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
+                                               const uint32_t *__restrict__ order,
+                                               const int64_t *__restrict__ eoffj, const int32_t *__restrict__ first,
+                                               int64_t m, uint64_t kappa, uint64_t ntiles,
+                                               int32_t *__restrict__ pinsj, uint32_t *__restrict__ jval) {
+    __shared__ int64_t s_off[kRelTile + 1];  // eoffj of the tile's edges
+    __shared__ int64_t s_src[kRelTile];      // eoff of their input edges
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t p0 = t * kRelTile;
+        const uint64_t p1 = p0 + kRelTile < kappa ? p0 + kRelTile : kappa;
+        const int64_t j0 = first[t];
+        const int64_t j1 = t + 1 < ntiles ? first[t + 1] : m - 1;  // last edge touching the tile
+        const int ne = (int)(j1 - j0 + 1);                          // <= kRelTile + 1
+        for (int k = threadIdx.x; k <= ne && k <= kRelTile; k += kT) {
+            s_off[k] = eoffj[j0 + k];
+            if (k < ne && k < kRelTile) s_src[k] = eoff[order[j0 + k]];
         }
+        __syncthreads();
+        const int hi0 = (ne < kRelTile ? ne : kRelTile) - 1;
+        for (uint64_t p = p0 + threadIdx.x; p < p1; p += kT) {
+            int lo = 0, hi = hi0;  // last k with s_off[k] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((uint64_t)s_off[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            pinsj[p] = pins[s_src[lo] + (int64_t)(p - (uint64_t)s_off[lo])];
+            jval[p] = (uint32_t)(j0 + lo);
+        }
+        __syncthreads();
     }
 }
 
@@ -131,6 +164,16 @@ __global__ void k_voff(const uint32_t *__restrict__ sv, const uint32_t *__restri
         }
         if (i > 0 && i < kappa && sv[i] == sv[i - 1] && vadj[i] == vadj[i - 1])
             report(err, kErrDup, 3, i);
+    }
+}
+
+// Constant half of the per-vertex record: list start and degree (the
+// mutable half, T[v] and its cursor, is reset by every match).
+__global__ void k_vrec_meta(const int64_t *__restrict__ voff, int64_t n, int4 *__restrict__ vrec) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = voff[v], e = voff[v + 1];
+        vrec[v] = make_int4(-2, 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
     }
 }
 
@@ -275,14 +318,22 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     tmp.drop(i64scratch);
     // val now receives j for every pin slot; the relabelled pins double as
     // the keys of the vertex sort
-    k_relabel<<<grid_for((uint64_t)m * 32, kT, h->sm_count, 16), kT, 0, s>>>(
-        eoff, pins, order_u, h->eoffj, m, h->pinsj, val);
+    {
+        const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;
+        int32_t *first = nullptr;
+        if ((st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK) return st;
+        k_tile_first<<<gm, kT, 0, s>>>(h->eoffj, m, ntiles, first);
+        k_relabel<<<grid_for(ntiles * kT, kT, h->sm_count, 8), kT, 0, s>>>(
+            eoff, pins, order_u, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
+        tmp.drop(first);
+    }
     cudaEventRecord(ev.e[3], s);
 
     // 4. vertex CSR: stable sort of (v, j) by v; keys land in `key`, values in vadj
     if ((st = dalloc(&h->vadj, kappa, s, "vadj")) != HM_OK ||
         (st = dalloc(&h->voff, (uint64_t)n + 1, s, "voff")) != HM_OK ||
-        (st = dalloc(&h->firstj, (uint64_t)n, s, "first entries")) != HM_OK)
+        (st = dalloc(&h->firstj, (uint64_t)n, s, "first entries")) != HM_OK ||
+        (st = dalloc(&h->vrec, (uint64_t)n, s, "vertex records")) != HM_OK)
         return st;
     const int vbits = bit_width(n > 0 ? (uint64_t)(n - 1) : 0);
     ce = radix_sort_pairs((const uint32_t *)h->pinsj, val, key, (uint32_t *)h->vadj, tk, tv, kappa,
@@ -290,6 +341,7 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     if (ce != cudaSuccess) return cuda_fail(ce, "vertex sort");
     k_voff<<<grid_for(kappa + 1, kT, h->sm_count, 16), kT, 0, s>>>(key, (const uint32_t *)h->vadj,
                                                                   kappa, n, h->voff, h->firstj, derr);
+    k_vrec_meta<<<grid_for((uint64_t)n, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, n, h->vrec);
     cudaEventRecord(ev.e[4], s);
     cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
     ce = cudaStreamSynchronize(s);

@@ -11,9 +11,11 @@
 //   alive  uint8[m]     1 = live edge (soft delete, Sec. 3.1)
 //   P      uint32[m]    pins of e that have not chosen e yet; e wins when it
 //                       reaches 0 (the P counter of Alg. 1 / Sec. 4.1, counted down)
-//   vst    int2[n]      per-vertex state {T[v] as an edge j, cursor of T[v]
-//                       relative to voff[v]} (Alg. 3's T); T[v] = kCurMatched
-//                       once v is covered, kCurNone when v has no live edge
+//   vrec   int4[n]      per-vertex record {T[v] as an edge j, cursor of T[v]
+//                       relative to the list start, list start, degree}
+//                       (Alg. 3's T plus V_id); T[v] = kCurMatched once v is
+//                       covered, kCurNone when v has no live edge. One 16-byte
+//                       load serves both the liveness check and the advance.
 //   firstj int32[n]     first entry of every vertex list (T[v] of round 1)
 //   list0/list1 int32[nregions*region] active vertex lists (ping-pong). The
 //                       list is cut into one region per warp of the argmax
@@ -73,7 +75,7 @@ struct RoundArgs {
     const int32_t *order;
     uint8_t *alive;
     uint32_t *P;
-    int2 *vst;
+    int4 *vrec;
     const int32_t *firstj;
     int32_t *list0;
     int32_t *list1;
@@ -110,7 +112,7 @@ struct Handle {
     float *weights = nullptr;   // input numbering, for the result weight
     uint8_t *alive = nullptr;
     uint32_t *P = nullptr;
-    int2 *vst = nullptr;
+    int4 *vrec = nullptr;
     int32_t *firstj = nullptr;
     int32_t *list0 = nullptr, *list1 = nullptr;
     uint32_t *lcnt = nullptr;

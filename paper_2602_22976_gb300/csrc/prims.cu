@@ -7,7 +7,7 @@ namespace hm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
+constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;  // 4096 elements per block
 constexpr int kWarps = kThreads / 32;
 static_assert(kThreads == 256, "histogram and scatter kernels use one thread per digit");
@@ -136,28 +136,33 @@ __global__ void __launch_bounds__(kThreads) rs_hist_k(const uint32_t *keys, uint
 // Stable scatter of one tile. Warp w owns the contiguous sub-tile
 // [w*512, (w+1)*512) and walks it 32 elements at a time; lanes with equal
 // digits are ranked with __match_any_sync, so equal keys keep input order
-// inside the warp, warps are ordered by a per-digit prefix over warps, and
-// tiles by the digit-major global offsets.
+// inside the warp, and warps are ordered by a per-digit prefix over warps.
+// The tile is first rearranged in shared memory into digit order, then
+// written out by consecutive threads, so each run of equal digits becomes
+// one coalesced segment of the output.
 __global__ void __launch_bounds__(kThreads) rs_scatter_k(const uint32_t *kin, const uint32_t *vin,
                                                          uint32_t *kout, uint32_t *vout, uint64_t n,
                                                          int shift, const uint32_t *offs,
                                                          uint32_t ntiles) {
     constexpr int kSub = 32 * kItems;
     __shared__ uint32_t wcnt[kWarps][256];
-    __shared__ uint32_t toff[256];
+    __shared__ uint32_t dstart[256];  // first tile-local slot of each digit
+    __shared__ uint32_t goff[256];    // global position of each digit's run from this tile
+    __shared__ uint32_t skey[kTile], sval[kTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < kWarps * 256; d += kThreads) (&wcnt[0][0])[d] = 0;
-    toff[threadIdx.x] = offs[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
+    goff[threadIdx.x] = offs[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
-    const uint64_t wbase = (uint64_t)blockIdx.x * kTile + (uint64_t)warp * kSub;
+    const uint64_t tbase = (uint64_t)blockIdx.x * kTile;
+    const uint32_t tcount = (uint32_t)(n - tbase < (uint64_t)kTile ? n - tbase : (uint64_t)kTile);
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[kItems], val[kItems], rank[kItems];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        const uint64_t i = wbase + (uint64_t)it * 32 + lane;
-        const bool ok = i < n;
-        key[it] = ok ? kin[i] : 0u;
-        val[it] = ok ? vin[i] : 0u;
+        const uint32_t li = (uint32_t)warp * kSub + it * 32 + lane;
+        const bool ok = li < tcount;
+        key[it] = ok ? kin[tbase + li] : 0u;
+        val[it] = ok ? vin[tbase + li] : 0u;
         const uint32_t d = ok ? ((key[it] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t base = d < 256u ? wcnt[warp][d] : 0u;
@@ -168,25 +173,36 @@ __global__ void __launch_bounds__(kThreads) rs_scatter_k(const uint32_t *kin, co
     }
     __syncthreads();
     {
+        // per digit: prefix over warps; per tile: prefix over digits
         const int d = threadIdx.x;
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            uint32_t t = wcnt[w][d];
+            const uint32_t t = wcnt[w][d];
             wcnt[w][d] = run;
             run += t;
         }
+        __shared__ uint32_t tot;
+        dstart[d] = block_exclusive_scan<uint32_t>(run, &tot);
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        const uint64_t i = wbase + (uint64_t)it * 32 + lane;
-        if (i < n) {
+        const uint32_t li = (uint32_t)warp * kSub + it * 32 + lane;
+        if (li < tcount) {
             const uint32_t d = (key[it] >> shift) & 255u;
-            const uint64_t pos = (uint64_t)toff[d] + wcnt[warp][d] + rank[it];
-            kout[pos] = key[it];
-            vout[pos] = val[it];
+            const uint32_t slot = dstart[d] + wcnt[warp][d] + rank[it];
+            skey[slot] = key[it];
+            sval[slot] = val[it];
         }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tcount; i += kThreads) {
+        const uint32_t k = skey[i];
+        const uint32_t d = (k >> shift) & 255u;
+        const uint64_t pos = (uint64_t)goff[d] + (i - dstart[d]);
+        kout[pos] = k;
+        vout[pos] = sval[i];
     }
 }
 

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
             a.P[i] = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
             a.inM[i] = 0;
         }
-        if (i < a.n) a.vst[i] = make_int2(a.firstj[i], 0);
+        if (i < a.n) reinterpret_cast<int2 *>(a.vrec + i)[0] = make_int2(a.firstj[i], 0);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevState *st = a.st;
@@ -170,17 +170,17 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
     int64_t vb = 0, from = 0, end = 0, cn = 0;
     int32_t jj = 0;
     if (ok) {
-        const int2 sv = a.vst[v];
-        if (sv.x >= 0) {
+        const int4 rec = a.vrec[v];
+        if (rec.x >= 0) {
             if (r == 1) {  // every edge is live in round 1: T[v] is the first entry
-                nb = sv.x;
+                nb = rec.x;
                 keep = true;
-            } else if (__ldg(alive + sv.x)) {
+            } else if (__ldg(alive + rec.x)) {
                 keep = true;  // T[v] still live: unchanged
             } else {
-                vb = __ldg(a.voff + v);
-                end = __ldg(a.voff + v + 1);
-                from = vb + sv.y;
+                vb = (int64_t)(uint32_t)rec.z;
+                end = vb + (int64_t)(uint32_t)rec.w;
+                from = vb + rec.y;
                 walk = true;
                 cn = next_live_bounded(vadj, alive, from + 1, end, jj);
                 coop = cn < 0;
@@ -214,12 +214,13 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
     }
     if (walk) {
         adv += (unsigned long long)(cn - from);
+        int2 *st2 = reinterpret_cast<int2 *>(a.vrec + v);
         if (cn < end) {
-            a.vst[v] = make_int2(jj, (int32_t)(cn - vb));
+            st2[0] = make_int2(jj, (int32_t)(cn - vb));
             nb = jj;
             keep = true;
         } else {
-            a.vst[v] = make_int2(kCurNone, 0);
+            st2[0] = make_int2(kCurNone, 0);
         }
     }
     return keep;
@@ -342,12 +343,12 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
             if (q < npins) {
                 const int w = last_le(s_wpre, kT - 1, q);
                 const int32_t v = __ldg(a.pinsj + s_wbeg[w] + (q - s_wpre[w]));
-                const int2 sv = a.vst[v];
-                c = __ldg(a.voff + v) + sv.y;
-                end = __ldg(a.voff + v + 1);
+                const int4 rec = a.vrec[v];
+                c = (int64_t)(uint32_t)rec.z + rec.y;
+                end = (int64_t)(uint32_t)rec.z + (int64_t)(uint32_t)rec.w;
                 // T[v] must be the winner: v chose it, and nothing moves it
-                if (sv.x == s_wj[w] && c < end) {
-                    a.vst[v] = make_int2(kCurMatched, 0);
+                if (rec.x == s_wj[w] && c < end) {
+                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurMatched, 0);
                     nch = (uint32_t)((end - c + kKillChunk - 1) / kKillChunk);
                     kills += (unsigned long long)(end - c);
                 } else {
@@ -386,9 +387,15 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
 
 // a3: deactivate every entry of every kill item. A warp takes one item
 // (<= kKillChunk entries) at a time; each lane has four entries in flight.
+// From round 2 on most targets are already dead (they sit behind the
+// cursors of other vertices), and on this GPU a random 1-byte load costs
+// less than half of a random 1-byte store, so the flag is read first and
+// only live targets are written. In round 1 every target is live: plain
+// stores.
 __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
     DevState *st = a.st;
     const uint64_t ni = min((uint64_t)st->nitems, a.item_cap);
+    const bool check = st->round > 1;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
@@ -401,10 +408,16 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
             const int32_t j1 = p + 32 < x.end ? __ldg(vadj + p + 32) : -1;
             const int32_t j2 = p + 64 < x.end ? __ldg(vadj + p + 64) : -1;
             const int32_t j3 = p + 96 < x.end ? __ldg(vadj + p + 96) : -1;
-            alive[j0] = 0;
-            if (j1 >= 0) alive[j1] = 0;
-            if (j2 >= 0) alive[j2] = 0;
-            if (j3 >= 0) alive[j3] = 0;
+            // a stale read can only show 1 for a flag another thread just
+            // cleared (flags only go 1 -> 0 here): then it is written twice
+            const bool w0 = !check || __ldcg(alive + j0) != 0;
+            const bool w1 = j1 >= 0 && (!check || __ldcg(alive + j1) != 0);
+            const bool w2 = j2 >= 0 && (!check || __ldcg(alive + j2) != 0);
+            const bool w3 = j3 >= 0 && (!check || __ldcg(alive + j3) != 0);
+            if (w0) alive[j0] = 0;
+            if (w1) alive[j1] = 0;
+            if (w2) alive[j2] = 0;
+            if (w3) alive[j3] = 0;
         }
     }
 }
@@ -466,10 +479,10 @@ __global__ void k_round_end(RoundArgs a) {
     if (a.use_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
 }
 
-__global__ void k_vertex_state(const int2 *vst, const int32_t *order, int64_t n, int32_t *out) {
+__global__ void k_vertex_state(const int4 *vrec, const int32_t *order, int64_t n, int32_t *out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t j = vst[v].x;
+        const int32_t j = vrec[v].x;
         out[v] = j >= 0 ? order[j] : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
     }
 }
@@ -595,7 +608,7 @@ RoundArgs round_args(const Handle *h) {
     a.order = h->order;
     a.alive = h->alive;
     a.P = h->P;
-    a.vst = h->vst;
+    a.vrec = h->vrec;
     a.firstj = h->firstj;
     a.list0 = h->list0;
     a.list1 = h->list1;
@@ -623,7 +636,10 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     hm_status st;
     if ((st = dalloc(&h->alive, m, s, "alive")) != HM_OK) return st;
     if ((st = dalloc(&h->P, m, s, "P")) != HM_OK) return st;
-    if ((st = dalloc(&h->vst, n, s, "vertex state")) != HM_OK) return st;
+    if (!h->vrec) {  // normally built by hm_create
+        set_error("vertex records missing");
+        return HM_EINVAL;
+    }
     // one list region per warp of the argmax grid
     h->argmax_grid = resident_grid(h, k_argmax);
     h->nregions = h->argmax_grid * (kT / 32);
@@ -705,14 +721,14 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
 }
 
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
-    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(h->vst, h->order, h->n,
+    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(h->vrec, h->order, h->n,
                                                                                 out_dev);
     return cudaGetLastError();
 }
 
 void free_handle_buffers(Handle *h) {
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
-                    h->vst, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->win, h->items, h->inM, h->stats, h->st,
+                    h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->win, h->items, h->inM, h->stats, h->st,
                     h->res_idx, h->res_w, h->res_part};
     for (void *p : bufs)
         if (p) cudaFree(p);

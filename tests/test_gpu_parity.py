@@ -183,6 +183,14 @@ def test_solve_host_matches_handle_path():
     assert np.array_equal(ru.edges, ou.edges) and ru.rounds == ou.rounds
 
 
+def test_random_access_probe():
+    r = hmlib.probe_random_access(1 << 20, 2_000_000)
+    assert set(r) == set(hmlib.PROBES) and all(v > 0 for v in r.values())
+    L = hmlib.lib()
+    out = np.zeros(5)
+    assert L.hm_probe_random_access(10, 1, out.ctypes.data, None) == EINVAL
+
+
 # ------------------------------------------------------------------ errors
 
 def _create(n, m, eoff, pins, w, flags=0):
