@@ -36,13 +36,16 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "large": dict(desc="powerlaw hypergraph n=10M m=20M |e|~Zipf(2)[2,1024] gamma=2.2 f32 w in (0,1]",
-                  make=lambda seed: __import__("synth").large(seed=seed),
+                  make=lambda seed, sc=1: __import__("synth").large(seed=seed, n=10_000_000 // sc,
+                                                                    m=20_000_000 // sc),
                   sample=lambda seed: __import__("synth").large(seed=seed, n=50_000, m=100_000)),
     "small": dict(desc="uniform hypergraph n=10k m=20k |e|~U{2..8} f32 w in (0,1]",
-                  make=lambda seed: __import__("synth").small(seed=seed),
+                  make=lambda seed, sc=1: __import__("synth").small(seed=seed, n=10_000 // sc,
+                                                                    m=20_000 // sc),
                   sample=lambda seed: __import__("synth").small(seed=seed)),
     "unweighted": dict(desc="uniform hypergraph n=4M m=8M |e|~U{2..8} unweighted, hash priority",
-                       make=lambda seed: __import__("synth").unweighted(seed=seed),
+                       make=lambda seed, sc=1: __import__("synth").unweighted(seed=seed, n=4_000_000 // sc,
+                                                                              m=8_000_000 // sc),
                        sample=lambda seed: __import__("synth").unweighted(seed=seed, n=40_000, m=80_000)),
 }
 METRIC = "pins/s (kappa*rounds/time)"
@@ -59,6 +62,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide n and m of the workload (smaller cases for profiler captures)")
     return ap.parse_args()
 
 
@@ -224,7 +229,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hm.build()
     wl = WORKLOADS[args.workload]
-    h = wl["make"](args.seed)
+    h = wl["make"](args.seed, args.scale)
     mt = hm.Matcher.from_hypergraph(h)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -328,7 +333,8 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": h.n, "m": h.m, "kappa": h.kappa,
+            "config": {"workload": wl["desc"] + (f" scaled 1/{args.scale}" if args.scale > 1 else ""),
+                       "n": h.n, "m": h.m, "kappa": h.kappa,
                        "rounds": res.rounds, "matched": res.count, "weight": res.weight,
                        "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps, outside step events",
                        "parallelism": f"replicas x{world}"},
