@@ -43,6 +43,7 @@ extern "C" {
 #endif
 
 typedef struct hm_handle hm_handle;
+typedef struct hm_batch hm_batch;
 
 typedef enum {
     HM_OK = 0,
@@ -57,6 +58,7 @@ typedef enum {
 #define HM_UNWEIGHTED   0x1u  /* ignore weights (may be NULL); priority = fmix32(e ^ s) */
 #define HM_BORROW_INPUT 0x2u  /* accepted for compatibility: inputs are never kept (see hm_create) */
 #define HM_VALIDATE     0x4u  /* accepted for compatibility: full validation always runs */
+#define HM_AUTOTUNE     0x8u  /* hm_batch_create: autotune every size class's launch shape */
 
 /*
  * hm_create - build a matching handle for one hypergraph.
@@ -116,6 +118,28 @@ hm_status hm_match(hm_handle *h, void *cuda_stream);
  * Errors: HM_EINVAL.
  */
 hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
+
+/*
+ * hm_launch_config - read and/or set the launch shape of the round kernels
+ * (no counterpart in the paper; the result never depends on it).
+ *   set  HOST int32[4] or NULL: {kill item size in list entries (64..2^20),
+ *        blocks per SM of the argmax, win and kill kernels (0 = as many as
+ *        fit)}; takes effect at the next hm_match
+ *   get  HOST int32[4] or NULL: the config in force
+ * Errors: HM_EINVAL.
+ */
+hm_status hm_launch_config(hm_handle *h, const int32_t *set, int32_t *get);
+
+/*
+ * hm_autotune - pick the launch shape of this handle by measurement: a
+ * coordinate-descent search over the kill item size and the blocks per SM
+ * of the three round kernels, each candidate timed as the median of three
+ * hm_match graph launches (CUDA events on `cuda_stream`). Leaves the best
+ * config applied and reports it (HOST int32[4], as hm_launch_config) and its
+ * time in ms. Runs about 40 matches; waits for them. The match result is
+ * the same under every config. Errors: as hm_match.
+ */
+hm_status hm_autotune(hm_handle *h, void *cuda_stream, int32_t *config_out, double *ms_out);
 
 /*
  * hm_result - wait for the last hm_match and report its result.
@@ -260,6 +284,58 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
 hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
                            const float *weights, uint64_t seed, uint32_t flags,
                            uint8_t *in_matching, int32_t *result, void *cuda_stream);
+
+/*
+ * hm_batch_create - many independent hypergraphs, matched together by one
+ * graph launch (no counterpart in the paper; it serves a preloaded set of
+ * hypergraphs inside a larger computation, the setting of Sec. 5.1).
+ *   count    number of instances (>= 1)
+ *   n, m     HOST int64[count]: vertices and edges of each instance
+ *   eoff     DEVICE int64[sum(m[i]+1)]: each instance's edge offsets as for
+ *            hm_create (starting at 0), concatenated in instance order
+ *   pins     DEVICE int32[sum(kappa_i)]: instance-local vertex ids, concatenated
+ *   weights  DEVICE float32[sum(m[i])], concatenated; NULL with HM_UNWEIGHTED
+ *   seed, flags  as hm_create, plus HM_AUTOTUNE
+ * Instances are grouped into size classes by kappa (factors of four); each
+ * class is matched as the disjoint union of its instances, and all classes
+ * are independent branches of one CUDA graph. Every instance gets exactly
+ * the matching and round count it would get from its own hm_create/hm_match
+ * (unweighted priorities use instance-local edge ids). With HM_AUTOTUNE each
+ * class's launch shape is chosen by hm_autotune's search. The inputs may be
+ * freed once the call returns (it synchronises `cuda_stream`).
+ * Errors: HM_EINVAL (as hm_create, per instance; a class beyond 2^31-1
+ * vertices or edges or 2^32-1 pins), HM_ENOMEM, HM_ECUDA.
+ */
+hm_status hm_batch_create(hm_batch **out, int32_t count, const int64_t *n, const int64_t *m,
+                          const int64_t *eoff, const int32_t *pins, const float *weights, uint64_t seed,
+                          uint32_t flags, void *cuda_stream);
+
+/* hm_batch_match - enqueue the whole batch (one graph launch); does not wait.
+ * Errors: HM_EINVAL, HM_EBUSY (running on another stream), HM_ECUDA. */
+hm_status hm_batch_match(hm_batch *b, void *cuda_stream);
+
+/*
+ * hm_batch_result - wait for the last hm_batch_match; per instance i:
+ *   edges_out    HOST int32[sum(m)] or NULL: instance-local matched edge ids,
+ *                ascending, instance after instance (instance i's block starts
+ *                at sum of counts_out[k] for k < i)
+ *   counts_out   HOST int64[count] or NULL: |M_i|
+ *   rounds_out   HOST int32[count] or NULL: rounds instance i takes alone
+ *   weights_out  HOST double[count] or NULL: w(M_i), float64 in ascending id
+ *                order (|M_i| when unweighted)
+ * Errors: HM_EINVAL, HM_ETIMEOUT / HM_EINVAL / HM_ECUDA if a class's loop did
+ * not finish cleanly (outputs are still written), HM_ECUDA.
+ */
+hm_status hm_batch_result(hm_batch *b, int32_t *edges_out, int64_t *counts_out, int32_t *rounds_out,
+                          double *weights_out);
+
+/* hm_batch_info - number of size classes, class of every instance (HOST
+ * int32[count] or NULL) and each class's launch shape (HOST
+ * int32[nclasses][4] or NULL, as hm_launch_config). Errors: HM_EINVAL. */
+hm_status hm_batch_info(hm_batch *b, int32_t *nclasses_out, int32_t *class_of, int32_t *configs);
+
+/* hm_batch_destroy - wait for outstanding work and free the batch. NULL is a no-op. */
+void hm_batch_destroy(hm_batch *b);
 
 /* hm_last_error - message of the last failure on this thread ("" if none). */
 const char *hm_last_error(void);

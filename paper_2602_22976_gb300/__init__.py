@@ -24,16 +24,18 @@ from . import build as _build
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ECUDA, HM_ETIMEOUT, HM_EBUSY = range(6)
 STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "HM_ETIMEOUT",
                 5: "HM_EBUSY"}
-HM_UNWEIGHTED, HM_BORROW_INPUT, HM_VALIDATE = 0x1, 0x2, 0x4
+HM_UNWEIGHTED, HM_BORROW_INPUT, HM_VALIDATE, HM_AUTOTUNE = 0x1, 0x2, 0x4, 0x8
 HM_VERTEX_MATCHED, HM_VERTEX_NONE = -1, -2
 STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills", "items", "next")
 KERNELS = ("init", "argmax", "win", "kill", "round_end")
 
 # Every entry point of include/hm.h, in declaration order.
-ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_result", "hm_result_device",
+ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_launch_config", "hm_autotune",
+                "hm_result", "hm_result_device",
                 "hm_round_stats", "hm_vertex_state", "hm_profile_match", "hm_create_ms",
-                "hm_probe_random_access", "hm_solve_host", "hm_match_noalloc", "hm_last_error",
-                "hm_destroy")
+                "hm_probe_random_access", "hm_solve_host", "hm_match_noalloc", "hm_batch_create",
+                "hm_batch_match", "hm_batch_result", "hm_batch_info", "hm_batch_destroy",
+                "hm_last_error", "hm_destroy")
 
 LIB_PATH = _build.LIB
 _lib = None
@@ -65,6 +67,8 @@ def lib() -> ctypes.CDLL:
             "hm_create": ([p, i64, i64, p, p, p, u64, u32, p], i32),
             "hm_match": ([p, p], i32),
             "hm_set_round_cap": ([p, i64], i32),
+            "hm_launch_config": ([p, p, p], i32),
+            "hm_autotune": ([p, p, p, p], i32),
             "hm_result": ([p, p, p, p, p], i32),
             "hm_result_device": ([p, p, p], i32),
             "hm_round_stats": ([p, p, i32, p], i32),
@@ -74,6 +78,11 @@ def lib() -> ctypes.CDLL:
             "hm_probe_random_access": ([u64, u64, p, p], i32),
             "hm_solve_host": ([i64, i64, p, p, p, u64, u32, p, p, p, p, p], i32),
             "hm_match_noalloc": ([i64, i64, p, p, p, u64, u32, p, p, p], i32),
+            "hm_batch_create": ([p, i32, p, p, p, p, p, u64, u32, p], i32),
+            "hm_batch_match": ([p, p], i32),
+            "hm_batch_result": ([p, p, p, p, p], i32),
+            "hm_batch_info": ([p, p, p, p], i32),
+            "hm_batch_destroy": ([p], None),
             "hm_last_error": ([], ctypes.c_char_p),
             "hm_destroy": ([p], None),
         }
@@ -161,6 +170,19 @@ class Matcher:
     def set_round_cap(self, cap: int) -> None:
         _check(lib().hm_set_round_cap(self.handle, int(cap)))
 
+    def launch_config(self, config=None) -> tuple:
+        """Set (kill_chunk, argmax_bpsm, win_bpsm, kill_bpsm) if given; return the one in force."""
+        get = np.zeros(4, dtype=np.int32)
+        st = None if config is None else np.asarray(config, dtype=np.int32)
+        _check(lib().hm_launch_config(self.handle, None if st is None else st.ctypes.data, get.ctypes.data))
+        return tuple(int(x) for x in get)
+
+    def autotune(self, stream=None) -> tuple[tuple, float]:
+        cfg = np.zeros(4, dtype=np.int32)
+        ms = ctypes.c_double(0.0)
+        _check(lib().hm_autotune(self.handle, _stream_handle(stream), cfg.ctypes.data, ctypes.byref(ms)))
+        return tuple(int(x) for x in cfg), ms.value
+
     def match(self, stream=None) -> None:
         _check(lib().hm_match(self.handle, _stream_handle(stream)))
 
@@ -207,6 +229,85 @@ class Matcher:
         if self._h is not None and _lib is not None:
             _lib.hm_destroy(self._h)
         self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent hypergraphs matched by one graph launch (hm_batch_*).
+
+    hgs: sequence of synth.Hypergraph-like objects (all weighted or all
+    unweighted, one seed). Inputs are concatenated and copied to the device.
+    """
+
+    def __init__(self, hgs, autotune: bool = False, stream=None, device: str = "cuda"):
+        import torch
+        self._b = None
+        self.count = len(hgs)
+        self.n = np.array([h.n for h in hgs], dtype=np.int64)
+        self.m = np.array([h.m for h in hgs], dtype=np.int64)
+        weighted = hgs[0].weights is not None
+        if any((h.weights is not None) != weighted for h in hgs):
+            raise ValueError("a batch is all weighted or all unweighted")
+        eoff = torch.from_numpy(np.concatenate([np.asarray(h.eoff, np.int64) for h in hgs])).to(device)
+        pins = torch.from_numpy(np.concatenate([np.asarray(h.pins, np.int32) for h in hgs])).to(device)
+        w = None
+        if weighted:
+            w = torch.from_numpy(np.concatenate([np.asarray(h.weights, np.float32) for h in hgs])).to(device)
+        torch.cuda.current_stream().synchronize()
+        flags = (0 if weighted else HM_UNWEIGHTED) | (HM_AUTOTUNE if autotune else 0)
+        b = ctypes.c_void_p()
+        st = lib().hm_batch_create(ctypes.byref(b), self.count, self.n.ctypes.data, self.m.ctypes.data,
+                                   eoff.data_ptr(), pins.data_ptr() if pins.numel() else None,
+                                   None if w is None else w.data_ptr(), hgs[0].seed, flags,
+                                   _stream_handle(stream))
+        _check(st)
+        self._b = b
+
+    @property
+    def handle(self) -> int:
+        if self._b is None:
+            raise RuntimeError("batch is closed")
+        return self._b.value
+
+    def match(self, stream=None) -> None:
+        _check(lib().hm_batch_match(self.handle, _stream_handle(stream)))
+
+    def result(self, allow=(HM_OK,)):
+        """Per instance: (edges int32 local ids, count, rounds, weight)."""
+        edges = np.empty(max(int(self.m.sum()), 1), dtype=np.int32)
+        counts = np.zeros(self.count, dtype=np.int64)
+        rounds = np.zeros(self.count, dtype=np.int32)
+        weights = np.zeros(self.count, dtype=np.float64)
+        st = lib().hm_batch_result(self.handle, edges.ctypes.data, counts.ctypes.data,
+                                   rounds.ctypes.data, weights.ctypes.data)
+        _check(st, allow)
+        offs = np.concatenate([[0], np.cumsum(counts)])
+        return [Result(edges[offs[i]:offs[i + 1]].copy(), int(counts[i]), int(rounds[i]),
+                       float(weights[i]), st) for i in range(self.count)]
+
+    def info(self) -> tuple[int, np.ndarray, np.ndarray]:
+        ncls = ctypes.c_int32(0)
+        _check(lib().hm_batch_info(self.handle, ctypes.byref(ncls), None, None))
+        cls = np.zeros(self.count, dtype=np.int32)
+        cfg = np.zeros((ncls.value, 4), dtype=np.int32)
+        _check(lib().hm_batch_info(self.handle, None, cls.ctypes.data, cfg.ctypes.data))
+        return ncls.value, cls, cfg
+
+    def close(self) -> None:
+        if self._b is not None and _lib is not None:
+            _lib.hm_batch_destroy(self._b)
+        self._b = None
 
     def __enter__(self):
         return self

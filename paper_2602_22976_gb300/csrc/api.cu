@@ -217,6 +217,54 @@ hm_status hm_profile_match(hm_handle *hh, void *cuda_stream, double *ms_out, int
     return st;
 }
 
+hm_status hm_launch_config(hm_handle *hh, const int32_t *set, int32_t *get) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (set) {
+        LaunchConfig c;
+        c.kill_chunk = set[0];
+        c.argmax_bpsm = set[1];
+        c.win_bpsm = set[2];
+        c.kill_bpsm = set[3];
+        hm_status st = apply_config(h, c);
+        if (st != HM_OK) return st;
+    }
+    if (get) {
+        get[0] = h->cfg.kill_chunk;
+        get[1] = h->cfg.argmax_bpsm;
+        get[2] = h->cfg.win_bpsm;
+        get[3] = h->cfg.kill_bpsm;
+    }
+    return HM_OK;
+}
+
+hm_status hm_autotune(hm_handle *hh, void *cuda_stream, int32_t *config_out, double *ms_out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    hm_status st = check_device(h);
+    if (st != HM_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (busy_check(h, s) != HM_OK) {
+        g_err = "a match of this handle is still running on another stream";
+        return HM_EBUSY;
+    }
+    LaunchConfig best;
+    double ms = 0;
+    st = autotune(h, s, &best, &ms);
+    if (st != HM_OK) return st;
+    cudaEventRecord(h->done, s);
+    h->last_stream = s;
+    h->matched_once = true;
+    if (config_out) {
+        config_out[0] = best.kill_chunk;
+        config_out[1] = best.argmax_bpsm;
+        config_out[2] = best.win_bpsm;
+        config_out[3] = best.kill_bpsm;
+    }
+    if (ms_out) *ms_out = ms;
+    return HM_OK;
+}
+
 hm_status hm_result(hm_handle *hh, int32_t *edges_out, int64_t *count_out, int32_t *rounds_out,
                     double *weight_out) {
     Handle *h = reinterpret_cast<Handle *>(hh);

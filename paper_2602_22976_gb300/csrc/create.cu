@@ -76,12 +76,25 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 }
 
 // Sort key = complemented priority (ascending sort = decreasing priority).
-// Positive finite floats order like their bit patterns.
+// Positive finite floats order like their bit patterns. For a union of
+// independent instances (inst_ebase != nullptr: first edge of each of the
+// ninst instances) the hash priority uses the edge's id inside its own
+// instance, so every instance is ordered exactly as it would be alone.
 __global__ void k_priority(const float *__restrict__ w, uint32_t salt, int64_t m,
+                           const int64_t *__restrict__ inst_ebase, int32_t ninst,
                            uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t prio = w ? __float_as_uint(w[e]) : fmix32((uint32_t)e ^ salt);
+        int64_t local = e;
+        if (!w && inst_ebase) {
+            int lo = 0, hi = ninst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (inst_ebase[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            local = e - inst_ebase[lo];
+        }
+        const uint32_t prio = w ? __float_as_uint(w[e]) : fmix32((uint32_t)local ^ salt);
         key[e] = ~prio;
         val[e] = (uint32_t)e;
     }
@@ -237,7 +250,8 @@ struct Temps {
 };
 
 hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
-                            const float *weights, cudaStream_t s) {
+                            const float *weights, cudaStream_t s, const int64_t *inst_ebase,
+                            int32_t ninst) {
     const int64_t n = h->n, m = h->m;
     const uint64_t kappa = h->kappa;
     struct Events {
@@ -298,7 +312,7 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
         return st;
     h->order = (int32_t *)order_u;  // owned by the handle from here on
     const uint32_t salt = (uint32_t)splitmix64_first(h->seed);
-    k_priority<<<gm, kT, 0, s>>>(h->weighted ? weights : nullptr, salt, m, key, val);
+    k_priority<<<gm, kT, 0, s>>>(h->weighted ? weights : nullptr, salt, m, inst_ebase, ninst, key, val);
     ce = radix_sort_pairs(key, val, sk, order_u, tk, tv, (uint64_t)m, 32, rscratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "priority sort");
     tmp.drop(sk);

@@ -25,7 +25,9 @@
 //   lcnt   uint32[2][nregions] region lengths
 //   wstage int32[nregions*region] per-region staging of a round's winners
 //   win    int32[min(m,n)] winners of the current round, contiguous
-//   items  KillItem[n + kappa/kKillChunk + 1] kill ranges of the current round
+//   items  KillItem[n + kappa/kMinKillChunk + 1] kill ranges of the current round
+//   wround int32[m]     round in which an edge joined M (input numbering; only
+//                       read for matched edges)
 //   inM    uint8[m]     result mask, input numbering
 #pragma once
 
@@ -40,7 +42,19 @@ namespace hm {
 
 constexpr int32_t kCurMatched = -1;  // vertex covered by the matching
 constexpr int32_t kCurNone = -2;     // vertex has no live edge (or degree 0)
-constexpr int kKillChunk = 256;      // max adjacency entries per kill item
+constexpr int kMinKillChunk = 64;    // smallest kill item size a launch config may use
+
+// Launch shape of the round kernels; the autotuner picks it per handle.
+struct LaunchConfig {
+    int kill_chunk = 256;  // max list entries per kill item
+    int argmax_bpsm = 0;   // blocks per SM of k_argmax (0 = all that fit)
+    int win_bpsm = 0;      // blocks per SM of k_win
+    int kill_bpsm = 0;     // blocks per SM of k_kill
+    bool operator==(const LaunchConfig &o) const {
+        return kill_chunk == o.kill_chunk && argmax_bpsm == o.argmax_bpsm && win_bpsm == o.win_bpsm &&
+               kill_bpsm == o.kill_bpsm;
+    }
+};
 constexpr int kStatRounds = 4096;    // per-round counters kept for this many rounds
 
 // Device-resident loop state (one per handle).
@@ -86,7 +100,9 @@ struct RoundArgs {
     int32_t *win;
     KillItem *items;
     uint8_t *inM;
+    int32_t *wround;
     int64_t *stats;        // [kStatRounds][HM_STATS_COLS]
+    int32_t kill_chunk;
     int64_t n;
     int64_t m;
     int64_t cap;           // round cap
@@ -118,7 +134,11 @@ struct Handle {
     uint32_t *lcnt = nullptr;
     int32_t *wstage = nullptr;
     uint32_t nregions = 0, region = 0;
-    unsigned argmax_grid = 0;
+    uint64_t list_cap = 0;     // entries in each of list0 / list1 / wstage
+    uint32_t regions_cap = 0;  // entries per parity in lcnt
+    unsigned argmax_grid = 0, win_grid = 0, kill_grid = 0;
+    LaunchConfig cfg, graph_cfg;
+    int32_t *wround = nullptr;
     int32_t *win = nullptr;
     KillItem *items = nullptr;
     uint8_t *inM = nullptr;
@@ -169,13 +189,22 @@ cudaError_t compact_flags(const uint8_t *flags, uint64_t n, const float *w, int3
                           float *w_out, uint32_t *part, cudaStream_t s);
 
 // ---- create (create.cu) ----
+// inst_ebase (device, ninst entries): first edge of each instance when the
+// input is a union of independent instances (local hash priorities), else null.
 hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
-                            const float *weights, cudaStream_t s);
+                            const float *weights, cudaStream_t s, const int64_t *inst_ebase = nullptr,
+                            int32_t ninst = 0);
 
 // ---- rounds (rounds.cu) ----
 RoundArgs round_args(const Handle *h);
 hm_status alloc_round_state(Handle *h, cudaStream_t s);
 hm_status launch_match_graph(Handle *h, cudaStream_t s);
+hm_status apply_config(Handle *h, const LaunchConfig &c);
+// Coordinate-descent search of the launch config; leaves the best applied.
+hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_ms);
+// Adds h's whole match (init node + conditional while loop) to graph g as a
+// branch with no dependencies.
+hm_status add_match_to_graph(Handle *h, cudaGraph_t g);
 hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches, double *round_ms,
                         int32_t max_rounds);
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);

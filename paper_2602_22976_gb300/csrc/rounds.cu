@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 namespace hm {
 namespace {
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
 }
 
 // a2: winners join M; every vertex of a winner is marked matched and emits
-// its list from the cursor on as kill items of <= kKillChunk entries.
+// its list from the cursor on as kill items of <= kill_chunk entries.
 // Blocks take kT winners at a time and spread their pins evenly over the
 // threads (prefix sum of edge sizes + binary search); item slots are
 // reserved with one atomic per kT pins and written by the whole block.
@@ -329,7 +330,9 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
             s_wbeg[t] = b;
             s_wj[t] = j;
             len = (uint32_t)(e - b);
-            a.inM[a.order[j]] = 1;
+            const int32_t ein = a.order[j];
+            a.inM[ein] = 1;
+            a.wround[ein] = st->round;
             winpins += len;
         }
         uint32_t npins;
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
                 // T[v] must be the winner: v chose it, and nothing moves it
                 if (rec.x == s_wj[w] && c < end) {
                     reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurMatched, 0);
-                    nch = (uint32_t)((end - c + kKillChunk - 1) / kKillChunk);
+                    nch = (uint32_t)((end - c + a.kill_chunk - 1) / a.kill_chunk);
                     kills += (unsigned long long)(end - c);
                 } else {
                     st->fault = 1;
@@ -373,8 +376,8 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
             if (ib != 0xFFFFFFFFu) {
                 for (uint32_t x = t; x < nitems; x += kT) {
                     const int pi = last_le(s_ipre, kT - 1, x);
-                    const int64_t lo = s_c[pi] + (int64_t)(x - s_ipre[pi]) * kKillChunk;
-                    const int64_t hi = lo + kKillChunk < s_end[pi] ? lo + kKillChunk : s_end[pi];
+                    const int64_t lo = s_c[pi] + (int64_t)(x - s_ipre[pi]) * a.kill_chunk;
+                    const int64_t hi = lo + a.kill_chunk < s_end[pi] ? lo + a.kill_chunk : s_end[pi];
                     a.items[(uint64_t)ib + x] = KillItem{lo, hi};
                 }
             }
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
 }
 
 // a3: deactivate every entry of every kill item. A warp takes one item
-// (<= kKillChunk entries) at a time; each lane has four entries in flight.
+// (<= kill_chunk entries) at a time; each lane has four entries in flight.
 // From round 2 on most targets are already dead (they sit behind the
 // cursors of other vertices), and on this GPU a random 1-byte load costs
 // less than half of a random 1-byte store, so the flag is read first and
@@ -489,30 +492,30 @@ __global__ void k_vertex_state(const int4 *vrec, const int32_t *order, int64_t n
 
 // Grid of a grid-stride round kernel: exactly the blocks that fit at once.
 template <typename K>
-unsigned resident_grid(const Handle *h, K kernel) {
+int max_blocks_per_sm(K kernel) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kT, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 4;
     }
-    return (unsigned)std::max(1, h->sm_count * per_sm);
+    return per_sm;
+}
+
+// blocks per SM actually used: the request, capped to what fits (0 = all)
+template <typename K>
+unsigned grid_of(const Handle *h, K kernel, int want) {
+    const int fit = max_blocks_per_sm(kernel);
+    const int b = want > 0 && want < fit ? want : fit;
+    return (unsigned)std::max(1, h->sm_count * b);
 }
 
 void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
-    static thread_local int cached_sms = -1;
-    static thread_local unsigned g_win = 0, g_kill = 0;
-    const unsigned g_arg = h->argmax_grid;
-    if (cached_sms != h->sm_count) {
-        g_win = resident_grid(h, k_win);
-        g_kill = resident_grid(h, k_kill);
-        cached_sms = h->sm_count;
-    }
     if (ev) cudaEventRecord(ev[0], s);
-    k_argmax<<<g_arg, kT, 0, s>>>(a);
+    k_argmax<<<h->argmax_grid, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[1], s);
-    k_win<<<g_win, kT, 0, s>>>(a);
+    k_win<<<h->win_grid, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
-    k_kill<<<g_kill, kT, 0, s>>>(a);
+    k_kill<<<h->kill_grid, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     k_round_end<<<1, 32, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[4], s);
@@ -537,30 +540,21 @@ hm_status dalloc(T **p, uint64_t count, cudaStream_t s, const char *what) {
     return HM_OK;
 }
 
-hm_status build_graph(Handle *h) {
+hm_status add_match_to_graph_impl(Handle *h, cudaGraph_t g) {
     cudaError_t e;
-    if (h->exec) {
-        cudaGraphExecDestroy(h->exec);
-        h->exec = nullptr;
-    }
     if (!h->cap_stream) {
         e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
     }
-    cudaGraph_t g = nullptr;
-    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
-    struct G {
-        cudaGraph_t g;
-        ~G() { cudaGraphDestroy(g); }
-    } guard{g};
     cudaGraphConditionalHandle cond;
     if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess)
         return cuda_fail(e, "cudaGraphConditionalHandleCreate");
     RoundArgs a = round_args(h);
     a.cond = cond;
     a.use_cond = 1;
-
-    // init node
+    // init node: captured with no dependencies, found as the one new root
+    size_t before = 0;
+    if ((e = cudaGraphGetNodes(g, nullptr, &before)) != cudaSuccess) return cuda_fail(e, "graph nodes");
     if ((e = cudaStreamBeginCaptureToGraph(h->cap_stream, g, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "capture (init)");
@@ -569,11 +563,20 @@ hm_status build_graph(Handle *h) {
     e = cudaStreamEndCapture(h->cap_stream, &out);
     if (e != cudaSuccess) return cuda_fail(e, "end capture (init)");
     size_t nn = 0;
-    cudaGraphNode_t init_node = nullptr;
-    if ((e = cudaGraphGetNodes(g, nullptr, &nn)) != cudaSuccess || nn != 1)
+    if ((e = cudaGraphGetNodes(g, nullptr, &nn)) != cudaSuccess || nn != before + 1)
         return cuda_fail(e == cudaSuccess ? cudaErrorUnknown : e, "graph init node");
-    if ((e = cudaGraphGetNodes(g, &init_node, &nn)) != cudaSuccess) return cuda_fail(e, "graph nodes");
-
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if ((e = cudaGraphGetNodes(g, nodes.data(), &nn)) != cudaSuccess) return cuda_fail(e, "graph nodes");
+    cudaGraphNode_t init_node = nullptr;
+    for (cudaGraphNode_t x : nodes) {  // the root that has no dependents yet and is a kernel
+        size_t ndep = 0, nout = 0;
+        cudaGraphNodeGetDependencies(x, nullptr, nullptr, &ndep);
+        cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &nout);
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(x, &t);
+        if (ndep == 0 && nout == 0 && t == cudaGraphNodeTypeKernel) init_node = x;
+    }
+    if (!init_node) return cuda_fail(cudaErrorUnknown, "graph init node not found");
     // while node around one round
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -590,9 +593,27 @@ hm_status build_graph(Handle *h) {
     launch_round(h, a, h->cap_stream, nullptr);
     e = cudaStreamEndCapture(h->cap_stream, &out);
     if (e != cudaSuccess) return cuda_fail(e, "end capture (round)");
+    return HM_OK;
+}
+
+hm_status build_graph(Handle *h) {
+    cudaError_t e;
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    struct G {
+        cudaGraph_t g;
+        ~G() { cudaGraphDestroy(g); }
+    } guard{g};
+    hm_status st = add_match_to_graph_impl(h, g);
+    if (st != HM_OK) return st;
     if ((e = cudaGraphInstantiate(&h->exec, g, 0)) != cudaSuccess)
         return cuda_fail(e, "cudaGraphInstantiate");
     h->graph_cap = h->cap;
+    h->graph_cfg = h->cfg;
     return HM_OK;
 }
 
@@ -624,6 +645,8 @@ RoundArgs round_args(const Handle *h) {
     a.m = h->m;
     a.cap = h->cap;
     a.item_cap = h->item_cap;
+    a.wround = h->wround;
+    a.kill_chunk = h->cfg.kill_chunk;
     a.win_cap = h->win_cap;
     a.use_cond = 0;
     return a;
@@ -632,7 +655,7 @@ RoundArgs round_args(const Handle *h) {
 hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
     h->win_cap = std::min(n, m) + 1;
-    h->item_cap = n + h->kappa / kKillChunk + 1;
+    h->item_cap = n + h->kappa / kMinKillChunk + 1;
     hm_status st;
     if ((st = dalloc(&h->alive, m, s, "alive")) != HM_OK) return st;
     if ((st = dalloc(&h->P, m, s, "P")) != HM_OK) return st;
@@ -640,19 +663,18 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
         set_error("vertex records missing");
         return HM_EINVAL;
     }
-    // one list region per warp of the argmax grid
-    h->argmax_grid = resident_grid(h, k_argmax);
-    h->nregions = h->argmax_grid * (kT / 32);
-    h->region = (uint32_t)((((n + h->nregions - 1) / h->nregions) + 31) / 32 * 32);
-    if (h->region == 0) h->region = 32;
-    const uint64_t lcap = (uint64_t)h->nregions * h->region;
-    if ((st = dalloc(&h->list0, lcap, s, "active list")) != HM_OK) return st;
-    if ((st = dalloc(&h->list1, lcap, s, "active list")) != HM_OK) return st;
-    if ((st = dalloc(&h->wstage, lcap, s, "winner staging")) != HM_OK) return st;
-    if ((st = dalloc(&h->lcnt, 2 * (uint64_t)h->nregions, s, "region lengths")) != HM_OK) return st;
+    // list regions: sized for the largest argmax grid any launch config can use
+    h->regions_cap = (uint32_t)(h->sm_count * max_blocks_per_sm(k_argmax) * (kT / 32));
+    h->list_cap = n + 32 * (uint64_t)h->regions_cap + 32;
+    if ((st = dalloc(&h->list0, h->list_cap, s, "active list")) != HM_OK) return st;
+    if ((st = dalloc(&h->list1, h->list_cap, s, "active list")) != HM_OK) return st;
+    if ((st = dalloc(&h->wstage, h->list_cap, s, "winner staging")) != HM_OK) return st;
+    if ((st = dalloc(&h->lcnt, 2 * (uint64_t)h->regions_cap, s, "region lengths")) != HM_OK) return st;
+    if ((st = dalloc(&h->wround, m, s, "win rounds")) != HM_OK) return st;
     if ((st = dalloc(&h->win, h->win_cap, s, "winners")) != HM_OK) return st;
     if ((st = dalloc(&h->items, h->item_cap, s, "kill items")) != HM_OK) return st;
     if ((st = dalloc(&h->inM, m, s, "result mask")) != HM_OK) return st;
+    if ((st = apply_config(h, h->cfg)) != HM_OK) return st;
     if ((st = dalloc(&h->stats, (uint64_t)kStatRounds * HM_STATS_COLS, s, "round stats")) != HM_OK) return st;
     if ((st = dalloc(&h->st, 1, s, "loop state")) != HM_OK) return st;
     if ((st = dalloc(&h->res_idx, m, s, "result ids")) != HM_OK) return st;
@@ -668,8 +690,28 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     return HM_OK;
 }
 
+hm_status apply_config(Handle *h, const LaunchConfig &c) {
+    if (c.kill_chunk < kMinKillChunk || c.kill_chunk > (1 << 20) || c.argmax_bpsm < 0 || c.win_bpsm < 0 ||
+        c.kill_bpsm < 0) {
+        set_error("launch config out of range");
+        return HM_EINVAL;
+    }
+    h->cfg = c;
+    h->argmax_grid = grid_of(h, k_argmax, c.argmax_bpsm);
+    h->win_grid = grid_of(h, k_win, c.win_bpsm);
+    h->kill_grid = grid_of(h, k_kill, c.kill_bpsm);
+    h->nregions = h->argmax_grid * (kT / 32);
+    if (h->nregions > h->regions_cap) h->nregions = h->regions_cap;
+    const uint64_t n = (uint64_t)h->n;
+    h->region = (uint32_t)((((n + h->nregions - 1) / h->nregions) + 31) / 32 * 32);
+    if (h->region == 0) h->region = 32;
+    return HM_OK;
+}
+
+hm_status add_match_to_graph(Handle *h, cudaGraph_t g) { return add_match_to_graph_impl(h, g); }
+
 hm_status launch_match_graph(Handle *h, cudaStream_t s) {
-    if (!h->exec || h->graph_cap != h->cap) {
+    if (!h->exec || h->graph_cap != h->cap || !(h->graph_cfg == h->cfg)) {
         hm_status st = build_graph(h);
         if (st != HM_OK) return st;
     }
@@ -720,6 +762,78 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
     return HM_OK;
 }
 
+// Median CUDA-event time of `reps` graph launches of h's match under config c.
+static hm_status time_config(Handle *h, cudaStream_t s, const LaunchConfig &c, int reps, double *ms) {
+    hm_status st = apply_config(h, c);
+    if (st != HM_OK) return st;
+    if ((st = launch_match_graph(h, s)) != HM_OK) return st;  // rebuild + warm-up
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> t;
+    for (int r = 0; r < reps && st == HM_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = launch_match_graph(h, s);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) st = cuda_fail(e, "autotune");
+        float x = 0;
+        cudaEventElapsedTime(&x, e0, e1);
+        t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HM_OK) return st;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return HM_OK;
+}
+
+hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_ms) {
+    LaunchConfig cur = h->cfg;
+    double cur_ms = 0;
+    hm_status st = time_config(h, s, cur, 3, &cur_ms);
+    if (st != HM_OK) return st;
+    auto consider = [&](LaunchConfig c) -> hm_status {
+        if (c == cur) return HM_OK;
+        double ms = 0;
+        hm_status r = time_config(h, s, c, 3, &ms);
+        if (r != HM_OK) return r;
+        if (ms < cur_ms) {
+            cur = c;
+            cur_ms = ms;
+        }
+        return HM_OK;
+    };
+    const int fit_arg = max_blocks_per_sm(k_argmax);
+    for (int pass = 0; pass < 2 && st == HM_OK; ++pass) {
+        for (int chunk : {64, 128, 256, 512, 1024}) {
+            LaunchConfig c = cur;
+            c.kill_chunk = chunk;
+            if ((st = consider(c)) != HM_OK) return st;
+        }
+        for (int b = fit_arg; b >= std::max(1, fit_arg - 3); --b) {
+            LaunchConfig c = cur;
+            c.argmax_bpsm = b == fit_arg ? 0 : b;
+            if ((st = consider(c)) != HM_OK) return st;
+        }
+        for (int b : {0, 4, 2}) {
+            LaunchConfig c = cur;
+            c.win_bpsm = b;
+            if ((st = consider(c)) != HM_OK) return st;
+        }
+        for (int b : {0, 4, 2}) {
+            LaunchConfig c = cur;
+            c.kill_bpsm = b;
+            if ((st = consider(c)) != HM_OK) return st;
+        }
+    }
+    if ((st = apply_config(h, cur)) != HM_OK) return st;
+    *best = cur;
+    *best_ms = cur_ms;
+    return HM_OK;
+}
+
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
     k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(h->vrec, h->order, h->n,
                                                                                 out_dev);
@@ -728,7 +842,7 @@ cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t 
 
 void free_handle_buffers(Handle *h) {
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
-                    h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->win, h->items, h->inM, h->stats, h->st,
+                    h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win, h->items, h->inM, h->stats, h->st,
                     h->res_idx, h->res_w, h->res_part};
     for (void *p : bufs)
         if (p) cudaFree(p);

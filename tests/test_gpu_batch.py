@@ -1,0 +1,100 @@
+"""Batched matching (hm_batch_*): every instance of a batch must get exactly
+the matching, round count and weight that the CPU oracle gives it alone."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2602_22976_gb300 as hmlib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    hmlib.build()
+    assert torch.cuda.is_available(), "needs a CUDA device"
+    hmlib.lib()
+
+
+def mixed_instances(seed, weighted=True, count=40):
+    rng = np.random.default_rng(seed)
+    hs = []
+    for i in range(count):
+        kind = i % 3
+        n = int(np.exp(rng.uniform(np.log(20), np.log(30_000))))
+        gs = seed * 1000 + i
+        if kind == 0:
+            h = synth.generate(n, 2 * n, kmin=2, kmax=16, weighted=weighted, seed=gs)
+        elif kind == 1:
+            h = synth.generate(max(n, 300), 2 * max(n, 300), size_dist=synth.SIZE_ZIPF, kmin=2, kmax=256,
+                               pin_dist=synth.PINS_POWERLAW, weighted=weighted, seed=gs)
+        else:
+            h = synth.generate(n, n // 2 + 1, kmin=1, kmax=6, weighted=weighted, seed=gs)
+        h.seed = seed  # one priority seed for the whole batch
+        hs.append(h)
+    return hs
+
+
+def check_against_oracle(hs, results):
+    assert len(results) == len(hs)
+    for h, r in zip(hs, results):
+        o = oracle.match(h)
+        assert r.status == hmlib.HM_OK
+        assert r.rounds == o.rounds, (h.name, r.rounds, o.rounds)
+        assert np.array_equal(r.edges, o.edges), h.name
+        assert r.weight == oracle.weight(h, o.in_matching)
+
+
+@pytest.mark.parametrize("weighted", [True, False])
+def test_batch_matches_solo_oracle(weighted):
+    hs = mixed_instances(3 if weighted else 4, weighted)
+    with hmlib.Batch(hs) as b:
+        ncls, cls, cfg = b.info()
+        assert ncls >= 2 and cls.shape == (len(hs),)
+        b.match()
+        check_against_oracle(hs, b.result())
+        b.match()  # a second launch recomputes the same result
+        check_against_oracle(hs, b.result())
+
+
+def test_batch_degenerate_members():
+    hs = [synth.from_edges(5, [], []),
+          synth.from_edges(3, [[0, 1, 2]], [0.5]),
+          synth.small(seed=2, n=500, m=1000),
+          synth.from_edges(8, [[i, i + 1] for i in range(7)], [(i + 1) / 8 for i in range(7)]),
+          synth.from_edges(1, [[0]], [1.0])]
+    for h in hs:
+        h.seed = 1
+    with hmlib.Batch(hs) as b:
+        b.match()
+        check_against_oracle(hs, b.result())
+
+
+def test_batch_autotuned_same_result():
+    hs = mixed_instances(5, True, count=24)
+    with hmlib.Batch(hs, autotune=True) as b:
+        ncls, _, cfg = b.info()
+        assert cfg.shape == (ncls, 4) and np.all(cfg[:, 0] >= 64)
+        b.match()
+        check_against_oracle(hs, b.result())
+
+
+def test_single_handle_autotune_and_config():
+    h = synth.large(seed=4, n=200_000, m=400_000)
+    o = oracle.match(h)
+    with hmlib.Matcher.from_hypergraph(h) as mt:
+        assert mt.launch_config() == (256, 0, 0, 0)
+        for cfg in [(64, 2, 2, 2), (1024, 0, 4, 0), (128, 1, 0, 4)]:
+            assert mt.launch_config(cfg) == cfg
+            mt.match()
+            r = mt.result()
+            assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+        best, ms = mt.autotune()
+        assert ms > 0 and best[0] in (64, 128, 256, 512, 1024)
+        mt.match()
+        r = mt.result()
+        assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+        with pytest.raises(hmlib.HMError):
+            mt.launch_config((8, 0, 0, 0))
