@@ -48,6 +48,9 @@ WORKLOADS = {
                                                                               m=8_000_000 // sc),
                        sample=lambda seed: __import__("synth").unweighted(seed=seed, n=40_000, m=80_000)),
 }
+WORKLOADS["batch"] = dict(
+    desc="4096 independent hypergraphs, n log-uniform in [100, 200000], m=2n, |e|~U{2..16}, f32 w",
+    make=None, sample=lambda seed: __import__("synth").batch(64, seed=seed))
 METRIC = "pins/s (kappa*rounds/time)"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -62,6 +65,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batch workload: skip the one-hm_match-per-instance comparison")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide n and m of the workload (smaller cases for profiler captures)")
     return ap.parse_args()
@@ -193,17 +198,21 @@ def run_reference(args, world, rank):
         return
     import oracle
     wl = WORKLOADS[args.workload]
-    h = wl["sample"](args.seed)
+    hs = wl["sample"](args.seed)
+    hs = hs if isinstance(hs, list) else [hs]
     oracle.build()
     for _ in range(args.warmup):
-        oracle.match(h)
+        for h in hs:
+            oracle.match(h)
     t0 = time.perf_counter()
-    rounds = 0
+    units = 0
     for _ in range(args.steps):
-        rounds = oracle.match(h).rounds
+        units = sum(h.kappa * oracle.match(h).rounds for h in hs)
     dt = time.perf_counter() - t0
-    value = h.kappa * rounds * args.steps / dt
-    sample = f"{h.name}: kappa={h.kappa}, rounds={rounds}, one oracle run per step"
+    value = units * args.steps / dt
+    sample = (f"{hs[0].name}: kappa={hs[0].kappa}, one oracle run per step" if len(hs) == 1 else
+              f"{len(hs)} instances of the batch generator, kappa={sum(h.kappa for h in hs)}, "
+              f"one oracle run of each per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
@@ -214,6 +223,87 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ batched arm
+
+def run_batch(args, world, rank, local):
+    """One step = one hm_batch_match over all instances (one graph launch);
+    compared with one hm_match per instance on the same GPU."""
+    import torch
+    import synth
+    import paper_2602_22976_gb300 as hm
+
+    torch.cuda.set_device(local)
+    hm.build()
+    count = max(1, 4096 // args.scale)
+    t0 = time.perf_counter()
+    hs = synth.batch(count, seed=args.seed + rank)
+    for h in hs:
+        h.seed = args.seed
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = hm.Batch(hs, autotune=True)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        b.match(stream)
+    res = b.result()
+    units_step = float(sum(h.kappa * r.rounds for h, r in zip(hs, res)))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        b.match(stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [x.elapsed_time(y) for x, y in zip(starts, ends)]
+    t_ms = float(sum(step_ms))
+    ncls, cls, cfg = b.info()
+    b.close()
+    # plain per-instance launches: one handle and one hm_match per instance
+    plain_ms = None
+    if not args.no_plain:
+        mts = [hm.Matcher.from_hypergraph(h) for h in hs]
+        for mt in mts:
+            mt.match(stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for mt in mts:
+            mt.match(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        for mt, r in zip(mts, res):
+            rr = mt.result()
+            assert rr.rounds == r.rounds and rr.count == r.count
+            mt.close()
+    out = {
+        "metric": METRIC, "value": units_step * args.steps / (t_ms / 1e3), "unit": "pins/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["batch"]["desc"] + (f" ({count} instances)" if count != 4096 else ""),
+                   "instances": count, "sum_kappa": int(sum(h.kappa for h in hs)),
+                   "sum_n": int(sum(h.n for h in hs)), "size_classes": int(ncls),
+                   "class_launch_configs": cfg.tolist(), "l2": "inputs larger than L2"},
+        "instances_per_s": count * args.steps / (t_ms / 1e3),
+        "time_to_matching_ms": {"median": statistics.median(step_ms)},
+        "create_s": t_create, "generate_s": t_gen,
+        "plain_per_instance": None if plain_ms is None else {
+            "ms": plain_ms, "value": units_step / (plain_ms / 1e3), "unit": "pins/s",
+            "batched_speedup": plain_ms / (t_ms / args.steps)},
+        "clocks": clk, "cpu_baseline": None, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------ our arm
@@ -375,6 +465,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batch":
+        run_batch(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 
