@@ -51,6 +51,11 @@ WORKLOADS = {
 WORKLOADS["batch"] = dict(
     desc="4096 independent hypergraphs, n log-uniform in [100, 200000], m=2n, |e|~U{2..16}, f32 w",
     make=None, sample=lambda seed: __import__("synth").batch(64, seed=seed))
+WORKLOADS["serve"] = dict(
+    desc="Poisson request stream, kappa log-uniform in [1e3,1e7], |e|~Zipf(2)[2,256], f32 w, "
+         "admitted by free HBM",
+    make=None, sample=lambda seed: [__import__("synth").serve_request(k, seed=seed * 1000 + i)
+                                    for i, k in enumerate([3000, 30000, 300000])])
 METRIC = "pins/s (kappa*rounds/time)"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -306,6 +311,80 @@ def run_batch(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ serving arm
+
+def run_serve(args, world, rank, local):
+    """Requests arrive as a Poisson stream at each rate of the sweep and go
+    through hm_server (continuous batching); latency = submit -> done."""
+    import torch
+    import synth
+    import paper_2602_22976_gb300 as hm
+
+    torch.cuda.set_device(local)
+    hm.build()
+    rng = np.random.default_rng(args.seed)
+    pool_n = max(8, 128 // args.scale)
+    kap = np.exp(rng.uniform(np.log(1e3), np.log(1e7 / args.scale), size=pool_n)).astype(np.int64)
+    pool = [synth.serve_request(int(k), seed=args.seed * 100_000 + i) for i, k in enumerate(kap)]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    arrays = [(pin(h.eoff), pin(h.pins), pin(h.weights)) for h in pool]
+    units = []  # kappa * rounds of every pool request (from a solo run)
+    for h in pool:
+        r = hm.solve_host(h)
+        units.append(h.kappa * r.rounds)
+
+    def run(rate, count, slots):
+        arr = synth.arrivals(count, rate, seed=args.seed + int(rate))
+        with hm.Server(slots=slots) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for i, ta in enumerate(arr):
+                while time.perf_counter() - t0 < ta:
+                    pass
+                k = i % pool_n
+                tickets.append((k, srv.submit(pool[k], arrays[k])))
+            lat = []
+            for k, t in tickets:
+                r, ms = srv.wait(t)
+                lat.append(ms)
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        work = float(sum(units[k] for k, _ in tickets))
+        return {"rate_req_s": rate, "requests": count, "slots": slots,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "pins_per_s": work / wall, "req_per_s": count / wall,
+                "peak_inflight": st["peak_inflight"], "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9}
+
+    slots = 8
+    sweep = []
+    clocks = Clocks(local)
+    clocks.start()
+    for rate in (100, 300, 1000, 3000, 10000):
+        count = int(min(max(64, rate * 1.0), 1000) // max(1, args.scale))
+        sweep.append(run(rate, max(count, 16), slots))
+    clk = clocks.stop()
+    # saturated throughput: the whole pool at once, served vs one request at a time
+    served = run(1e9, 2 * pool_n, slots)
+    serial = run(1e9, 2 * pool_n, 1)
+    out = {
+        "metric": METRIC, "value": served["pins_per_s"], "unit": "pins/s", "n_gpus": world,
+        "steps": 2 * pool_n, "warmup": 0, "ms_per_step": 1e3 / served["req_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["serve"]["desc"], "pool": pool_n, "slots": slots,
+                   "kappa_mean": float(kap.mean()), "l2": "inputs larger than L2"},
+        "sweep": sweep, "saturated_served": served, "saturated_one_slot": serial,
+        "served_speedup": served["pins_per_s"] / serial["pins_per_s"],
+        "clocks": clk, "cpu_baseline": None,
+        "e2e": {"value": served["pins_per_s"], "unit": "pins/s",
+                "h2d_bytes_per_step": int(np.mean([h.eoff.nbytes + h.pins.nbytes + h.weights.nbytes
+                                                   for h in pool])),
+                "d2h_bytes_per_step": None},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, world, rank, local):
@@ -467,6 +546,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batch":
         run_batch(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -44,6 +44,7 @@ extern "C" {
 
 typedef struct hm_handle hm_handle;
 typedef struct hm_batch hm_batch;
+typedef struct hm_server hm_server;
 
 typedef enum {
     HM_OK = 0,
@@ -336,6 +337,48 @@ hm_status hm_batch_info(hm_batch *b, int32_t *nclasses_out, int32_t *class_of, i
 
 /* hm_batch_destroy - wait for outstanding work and free the batch. NULL is a no-op. */
 void hm_batch_destroy(hm_batch *b);
+
+/*
+ * hm_server_create - a request loop with continuous batching (no
+ * counterpart in the paper). `slots` worker threads, each with its own CUDA
+ * stream on the current device, take requests from a FIFO queue; the queue
+ * head is admitted as soon as a slot is free and its estimated device
+ * footprint (36*kappa + 64*m + 72*n bytes + 16 MiB) fits under the budget:
+ * `hbm_budget_bytes`, capped at 90 % of the free device memory at creation
+ * (0 = that cap). Admitted requests run the hm_solve_host path on their
+ * worker's stream, so requests arriving while others are on the GPU overlap
+ * with them, and each gets the same result as alone.
+ * Errors: HM_EINVAL (slots outside [1, 256]), HM_ENOMEM, HM_ECUDA.
+ */
+hm_status hm_server_create(hm_server **out, int32_t slots, uint64_t hbm_budget_bytes);
+
+/*
+ * hm_server_submit - queue one request: HOST eoff/pins/weights as for
+ * hm_solve_host (pinned host memory gives full copy bandwidth). The caller
+ * keeps the three arrays unchanged until hm_server_wait returns for the
+ * ticket. Returns at once with a ticket (> 0).
+ * Errors: HM_EINVAL (sizes, eoff), HM_ENOMEM (the request alone exceeds the
+ * budget). Input errors found on the device are reported by hm_server_wait.
+ */
+hm_status hm_server_submit(hm_server *s, int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
+                           const float *weights, uint64_t seed, uint32_t flags, int64_t *ticket_out);
+
+/*
+ * hm_server_wait - wait for a ticket and collect its result (once): outputs
+ * as hm_result (edges_out HOST int32[m] or NULL), plus latency_ms_out (may
+ * be NULL): milliseconds from hm_server_submit to completion.
+ * Errors: HM_EINVAL (unknown ticket), or the request's own status.
+ */
+hm_status hm_server_wait(hm_server *s, int64_t ticket, int32_t *edges_out, int64_t *count_out,
+                         int32_t *rounds_out, double *weight_out, double *latency_ms_out);
+
+/* hm_server_stats - HOST int64[7]: completed, queued, in flight, peak in
+ * flight, reserved bytes, peak reserved bytes, budget. Errors: HM_EINVAL. */
+hm_status hm_server_stats(hm_server *s, int64_t *stats_out);
+
+/* hm_server_destroy - finish every submitted request, stop the workers and
+ * free the server (results not yet collected are dropped). NULL is a no-op. */
+void hm_server_destroy(hm_server *s);
 
 /* hm_last_error - message of the last failure on this thread ("" if none). */
 const char *hm_last_error(void);

@@ -35,7 +35,8 @@ ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_launch_config",
                 "hm_round_stats", "hm_vertex_state", "hm_profile_match", "hm_create_ms",
                 "hm_probe_random_access", "hm_solve_host", "hm_match_noalloc", "hm_batch_create",
                 "hm_batch_match", "hm_batch_result", "hm_batch_info", "hm_batch_destroy",
-                "hm_last_error", "hm_destroy")
+                "hm_server_create", "hm_server_submit", "hm_server_wait", "hm_server_stats",
+                "hm_server_destroy", "hm_last_error", "hm_destroy")
 
 LIB_PATH = _build.LIB
 _lib = None
@@ -83,6 +84,11 @@ def lib() -> ctypes.CDLL:
             "hm_batch_result": ([p, p, p, p, p], i32),
             "hm_batch_info": ([p, p, p, p], i32),
             "hm_batch_destroy": ([p], None),
+            "hm_server_create": ([p, i32, u64], i32),
+            "hm_server_submit": ([p, i64, i64, p, p, p, u64, u32, p], i32),
+            "hm_server_wait": ([p, i64, p, p, p, p, p], i32),
+            "hm_server_stats": ([p, p], i32),
+            "hm_server_destroy": ([p], None),
             "hm_last_error": ([], ctypes.c_char_p),
             "hm_destroy": ([p], None),
         }
@@ -308,6 +314,77 @@ class Batch:
         if self._b is not None and _lib is not None:
             _lib.hm_batch_destroy(self._b)
         self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SERVER_STATS = ("completed", "queued", "inflight", "peak_inflight", "reserved_bytes",
+                "peak_reserved_bytes", "budget_bytes")
+
+
+class Server:
+    """hm_server: requests from host arrays, continuous batching on the GPU."""
+
+    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 0):
+        self._s = None
+        self._keep: dict[int, tuple] = {}
+        s = ctypes.c_void_p()
+        _check(lib().hm_server_create(ctypes.byref(s), int(slots), int(hbm_budget_bytes)))
+        self._s = s
+
+    @property
+    def handle(self) -> int:
+        if self._s is None:
+            raise RuntimeError("server is closed")
+        return self._s.value
+
+    def submit(self, hg, arrays=None) -> int:
+        """Queue hypergraph `hg`; `arrays` = (eoff, pins, weights) host arrays to
+        use instead of hg's (e.g. pinned). They are kept alive until wait()."""
+        if arrays is None:
+            arrays = (np.ascontiguousarray(hg.eoff, np.int64), np.ascontiguousarray(hg.pins, np.int32),
+                      None if hg.weights is None else np.ascontiguousarray(hg.weights, np.float32))
+        ptr = lambda a: None if a is None else (a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        eoff, pins, w = arrays
+        flags = HM_UNWEIGHTED if w is None else 0
+        t = ctypes.c_int64(0)
+        _check(lib().hm_server_submit(self.handle, hg.n, hg.m, ptr(eoff), ptr(pins), ptr(w), hg.seed,
+                                      flags, ctypes.byref(t)))
+        self._keep[t.value] = (arrays, hg.m)
+        return t.value
+
+    def wait(self, ticket: int, allow=(HM_OK,)) -> tuple[Result, float]:
+        arrays, m = self._keep.pop(ticket)
+        edges = np.empty(max(m, 1), dtype=np.int32)
+        count = ctypes.c_int64(0)
+        rounds = ctypes.c_int32(0)
+        weight = ctypes.c_double(0.0)
+        lat = ctypes.c_double(0.0)
+        st = lib().hm_server_wait(self.handle, ticket, edges.ctypes.data, ctypes.byref(count),
+                                  ctypes.byref(rounds), ctypes.byref(weight), ctypes.byref(lat))
+        _check(st, allow)
+        return Result(edges[:count.value].copy(), count.value, rounds.value, weight.value, st), lat.value
+
+    def stats(self) -> dict:
+        out = np.zeros(len(SERVER_STATS), dtype=np.int64)
+        _check(lib().hm_server_stats(self.handle, out.ctypes.data))
+        return dict(zip(SERVER_STATS, out.tolist()))
+
+    def close(self) -> None:
+        if self._s is not None and _lib is not None:
+            _lib.hm_server_destroy(self._s)
+        self._s = None
+        self._keep.clear()
 
     def __enter__(self):
         return self

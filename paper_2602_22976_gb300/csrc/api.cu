@@ -143,15 +143,14 @@ hm_status hm_create(hm_handle **out, int64_t n, int64_t m, const int64_t *eoff, 
     }
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     raise_pool_threshold(h->device);
-    hm_status st = create_structures(h, eoff, pins, weights, s);
+    hm_status st = HM_OK;
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        st = cuda_fail(e, "cudaStreamCreate");
+    if (st == HM_OK) st = create_structures(h, eoff, pins, weights, s);
     if (st == HM_OK) st = alloc_round_state(h, s);
     if (st == HM_OK) {
         if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess)
             st = cuda_fail(e, "cudaEventCreate");
-    }
-    if (st == HM_OK) {
-        if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-            st = cuda_fail(e, "cudaStreamCreate");
     }
     if (st == HM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "hm_create");
     if (st != HM_OK) {

@@ -186,12 +186,13 @@ hm_status build_class(Batch *b, BatchClass &c, const int64_t *eoff, const int32_
             h->cap = m_u + 1;
             h->device = b->device;
             h->sm_count = sm_count;
-            st = create_structures(h, eoff_u, pins_u, w_u, s, b->weighted ? nullptr : d_ub, nmem);
+            if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+                st = cuda_fail(e, "cudaStreamCreate");
+            if (st == HM_OK)
+                st = create_structures(h, eoff_u, pins_u, w_u, s, b->weighted ? nullptr : d_ub, nmem);
             if (st == HM_OK) st = alloc_round_state(h, s);
             if (st == HM_OK && (e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess)
                 st = cuda_fail(e, "cudaEventCreate");
-            if (st == HM_OK && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-                st = cuda_fail(e, "cudaStreamCreate");
         }
     }
     if (d_mem) cudaFreeAsync(d_mem, s);

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <new>
 #include <vector>
 
 namespace hm {
@@ -682,9 +683,9 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     if ((st = dalloc(&h->res_part, compact_scratch_elems(m) + 1, s, "result scratch")) != HM_OK) return st;
     cudaError_t e = cudaMemsetAsync(h->stats, 0, (size_t)kStatRounds * HM_STATS_COLS * sizeof(int64_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "stats reset");
-    if (cudaMallocHost((void **)&h->h_st, sizeof(DevState)) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("out of pinned host memory");
+    h->h_st = new (std::nothrow) DevState();
+    if (!h->h_st) {
+        set_error("out of host memory");
         return HM_ENOMEM;
     }
     return HM_OK;
@@ -840,13 +841,18 @@ cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Stream-ordered frees on the handle's own stream: cudaFree would wait for
+// the whole device, stalling every other stream (other handles, requests).
 void free_handle_buffers(Handle *h) {
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
-                    h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win, h->items, h->inM, h->stats, h->st,
-                    h->res_idx, h->res_w, h->res_part};
+                    h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win,
+                    h->items, h->inM, h->stats, h->st, h->res_idx, h->res_w, h->res_part};
+    cudaStream_t s = h->cap_stream;
     for (void *p : bufs)
-        if (p) cudaFree(p);
-    if (h->h_st) cudaFreeHost(h->h_st);
+        if (p) cudaFreeAsync(p, s);
+    if (s) cudaStreamSynchronize(s);
+    delete h->h_st;
+    h->h_st = nullptr;
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->done) cudaEventDestroy(h->done);
