@@ -32,7 +32,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     out = lib_path(mutant)
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
         tmp = out + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-std=c11",
+        subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-std=c11", "-ffp-contract=off",
                         f"-DORACLE_MUTANT={mutant}", _SRC, "-o", tmp], check=True)
         os.replace(tmp, out)
     return out
@@ -48,7 +48,11 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
         lib.oracle_fmix32.restype = ctypes.c_uint32
         lib.oracle_key.argtypes = [p, i32, u64, i64]
         lib.oracle_key.restype = u64
-        lib.oracle_match.argtypes = [i64, i64, p, p, p, i32, u64, i64, p, p, p, p, p, p]
+        lib.oracle_splitmix64_at.argtypes = [u64, u64]
+        lib.oracle_splitmix64_at.restype = u64
+        lib.oracle_round_priority.argtypes = [p, i32, u64, ctypes.c_float, i64, i64]
+        lib.oracle_round_priority.restype = ctypes.c_float
+        lib.oracle_match.argtypes = [i64, i64, p, p, p, i32, u64, ctypes.c_float, i64, p, p, p, p, p, p]
         lib.oracle_match.restype = i32
         lib.oracle_greedy.argtypes = [i64, i64, p, p, p, i32, u64, p]
         lib.oracle_greedy.restype = i32
@@ -57,7 +61,7 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
         for name in ("oracle_check_disjoint", "oracle_check_maximal"):
             getattr(lib, name).argtypes = [i64, i64, p, p, p]
             getattr(lib, name).restype = i64
-        lib.oracle_check_local_max.argtypes = [i64, i64, p, p, p, i32, u64, p, p]
+        lib.oracle_check_local_max.argtypes = [i64, i64, p, p, p, i32, u64, ctypes.c_float, p, p]
         lib.oracle_check_local_max.restype = i64
         _libs[mutant] = lib
     return _libs[mutant]
@@ -89,9 +93,10 @@ class Result:
         return np.flatnonzero(self.in_matching).astype(np.int32)
 
 
-def match(h, max_rounds: int | None = None, mutant: int = 0) -> Result:
+def match(h, max_rounds: int | None = None, mutant: int = 0, noise: float = 0.0) -> Result:
     """Run the rounds on hypergraph ``h`` (a ``synth.Hypergraph``-like object
-    with n, m, eoff, pins, weights (None = unweighted) and seed)."""
+    with n, m, eoff, pins, weights (None = unweighted) and seed). noise > 0:
+    priorities re-drawn before every round, amplitude `noise`."""
     lib = _load(mutant)
     eoff, pins, w = _inputs(h)
     cap = h.m + 1 if max_rounds is None else int(max_rounds)
@@ -101,7 +106,7 @@ def match(h, max_rounds: int | None = None, mutant: int = 0) -> Result:
     best = np.zeros(max(h.n, 1), dtype=np.int32)
     matched = np.zeros(max(h.n, 1), dtype=np.uint8)
     rounds = ctypes.c_int(0)
-    rc = lib.oracle_match(h.n, h.m, _p(eoff), _p(pins), _p(w), int(w is None), h.seed, cap,
+    rc = lib.oracle_match(h.n, h.m, _p(eoff), _p(pins), _p(w), int(w is None), h.seed, float(noise), cap,
                           _p(inm), _p(dec), _p(stats), ctypes.addressof(rounds), _p(best),
                           _p(matched))
     if rc < 0:
@@ -149,12 +154,12 @@ def check_maximal(h, in_matching) -> int:
     return int(_load().oracle_check_maximal(h.n, h.m, _p(eoff), _p(pins), _p(inm)))
 
 
-def check_local_max(h, in_matching, decided_round) -> int:
+def check_local_max(h, in_matching, decided_round, noise: float = 0.0) -> int:
     eoff, pins, w = _inputs(h)
     inm = np.ascontiguousarray(in_matching, dtype=np.uint8)
     dec = np.ascontiguousarray(decided_round, dtype=np.int32)
     return int(_load().oracle_check_local_max(h.n, h.m, _p(eoff), _p(pins), _p(w),
-                                              int(w is None), h.seed, _p(inm), _p(dec)))
+                                              int(w is None), h.seed, float(noise), _p(inm), _p(dec)))
 
 
 def keys(h) -> np.ndarray:
@@ -167,6 +172,15 @@ def keys(h) -> np.ndarray:
 
 def splitmix64_first(seed: int) -> int:
     return int(_load().oracle_splitmix64_first(seed))
+
+
+def splitmix64_at(s0: int, k: int) -> int:
+    return int(_load().oracle_splitmix64_at(s0, k))
+
+
+def round_priority(h, noise: float, r: int, e: int) -> float:
+    _, _, w = _inputs(h)
+    return float(_load().oracle_round_priority(_p(w), int(w is None), h.seed, noise, r, e))
 
 
 def fmix32(x: int) -> int:

@@ -23,7 +23,13 @@
  * equal weight -> smaller edge id wins". fmix32 is the MurmurHash3 32-bit
  * finaliser (Appleby); SplitMix64 is from Steele, Lea, Flood (OOPSLA 2014).
  * The paper instead re-draws random weights every round (Sec. 3.1, Sec. 5.1);
- * the fixed order makes the result unique and so exactly comparable.
+ * the fixed order makes the result unique and so exactly comparable. With
+ * noise > 0 the rounds follow the paper instead: before round r every edge
+ * gets the priority p_r(e) = base_e + noise * U_r(e) in float32 arithmetic
+ * (base_e = w_e, or 1.0f for unweighted input; U_r(e) in [0,1) is the top 24
+ * bits of output number (r << 32) + e + 1 of a SplitMix64 stream whose
+ * state starts at the first SplitMix64 output for `seed`, times 2^-24), and
+ * key_r(e) = (bits(p_r(e)) << 32) | (0xFFFFFFFF - e).
  *
  * Also here: the sequential greedy algorithm (sort by key, take an edge when
  * all its vertices are free; the paper's single-core baseline, Sec. 5.2),
@@ -62,6 +68,15 @@ uint32_t oracle_fmix32(uint32_t h)
     return h;
 }
 
+/* Output number k (k >= 1) of SplitMix64 started at state s0. */
+uint64_t oracle_splitmix64_at(uint64_t s0, uint64_t k)
+{
+    uint64_t z = s0 + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
 static uint32_t float_bits(float f)
 {
     uint32_t u;
@@ -81,6 +96,23 @@ uint64_t oracle_key(const float *w, int unweighted, uint64_t seed, int64_t e)
 #else
     return ((uint64_t)float_bits(w[e]) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)e);
 #endif
+}
+
+/* Per-round priority p_r(e) of the re-randomised rounds (see header). */
+float oracle_round_priority(const float *w, int unweighted, uint64_t seed, float noise, int64_t r, int64_t e)
+{
+    uint64_t s0 = oracle_splitmix64_first(seed);
+    uint64_t h = oracle_splitmix64_at(s0, ((uint64_t)r << 32) + (uint64_t)e + 1u);
+    float u24 = (float)(uint32_t)(h >> 40);
+    float scaled = u24 * (noise * (1.0f / 16777216.0f));
+    float base = unweighted ? 1.0f : w[e];
+    return base + scaled;
+}
+
+static uint64_t round_key(const float *w, int unweighted, uint64_t seed, float noise, int64_t r, int64_t e)
+{
+    float p = oracle_round_priority(w, unweighted, seed, noise, r, e);
+    return ((uint64_t)float_bits(p) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)e);
 }
 
 static uint64_t *all_keys(int64_t m, const float *w, int unweighted, uint64_t seed)
@@ -106,11 +138,13 @@ static uint64_t *all_keys(int64_t m, const float *w, int unweighted, uint64_t se
  *                     largest key among v's live edges at the start of that
  *                     round, or -2 if v had none (NULL allowed)
  *   matched_out[n]    1 if v is covered by M after the last round (NULL allowed)
+ * noise == 0: one fixed order for the whole run; noise > 0: priorities
+ * re-drawn before every round (see header).
  * max_rounds <= 0 means no cap. Returns 0 when every edge is decided, 1 when
  * the cap stopped the loop first, -1 on allocation failure.
  */
 int oracle_match(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
-                 const float *w, int unweighted, uint64_t seed, int64_t max_rounds,
+                 const float *w, int unweighted, uint64_t seed, float noise, int64_t max_rounds,
                  uint8_t *in_matching, int32_t *decided_round, int64_t *round_stats,
                  int32_t *rounds_out, int32_t *best_edge_out, uint8_t *matched_out)
 {
@@ -138,6 +172,13 @@ int oracle_match(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
         if (max_rounds > 0 && r >= max_rounds) { status = 1; break; }
         r += 1;
         int64_t live_pins = 0;
+#if ORACLE_MUTANT == 6 /* priorities drawn once, not before every round */
+        if (noise > 0.0f && r == 1)
+#else
+        if (noise > 0.0f) /* re-draw the priorities of the live edges */
+#endif
+            for (int64_t e = 0; e < m; ++e)
+                if (alive[e]) key[e] = round_key(w, unweighted, seed, noise, r, e);
         /* step 1: best[v] = max key over live edges containing v */
         for (int64_t v = 0; v < n; ++v) { best[v] = NONE; best_e[v] = -2; }
         for (int64_t e = 0; e < m; ++e) {
@@ -333,12 +374,13 @@ int64_t oracle_check_maximal(int64_t n, int64_t m, const int64_t *eoff, const in
 
 /* Local maximality (Sec. 2.1 "locally maximal"; Sec. 3.1): an edge matched in
  * round r is heavier than every edge sharing a vertex with it that was still
- * live at the start of round r (decided in round >= r). Checked vertex by
+ * live at the start of round r (decided in round >= r), under the keys of
+ * round r (the fixed keys when noise == 0). Checked vertex by
  * vertex: the matched edge at v must carry the largest key among the edges
  * at v decided in its round or later. Returns -1 if it holds, else the index
  * of an offending vertex. O(kappa) time. */
 int64_t oracle_check_local_max(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
-                               const float *w, int unweighted, uint64_t seed,
+                               const float *w, int unweighted, uint64_t seed, float noise,
                                const uint8_t *in_matching, const int32_t *decided_round)
 {
     uint64_t *key = all_keys(m, w, unweighted, seed);
@@ -353,7 +395,17 @@ int64_t oracle_check_local_max(int64_t n, int64_t m, const int64_t *eoff, const 
         for (int64_t i = eoff[f]; i < eoff[f + 1]; ++i) {
             int64_t v = pins[i], e = mate[v];
             if (e < 0 || e == f) continue;
-            if (decided_round[f] >= decided_round[e] && key[f] > key[e]) { bad = v; break; }
+            if (decided_round[f] < decided_round[e]) continue;
+            if (noise > 0.0f) {
+                int64_t r = decided_round[e];
+                if (round_key(w, unweighted, seed, noise, r, f) > round_key(w, unweighted, seed, noise, r, e)) {
+                    bad = v;
+                    break;
+                }
+            } else if (key[f] > key[e]) {
+                bad = v;
+                break;
+            }
         }
     }
     free(key); free(mate);

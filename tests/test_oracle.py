@@ -271,3 +271,76 @@ def test_pins_reject_planted_mistakes(mutant):
     # 1 reversed tie-break, 2 argmin for argmax, 3 one vertex consulted,
     # 4 no deactivation step, 5 dead edges keep competing
     assert not _pins_pass(mutant)
+
+
+# ---------------------------------------------------------------- re-randomised rounds
+
+def test_splitmix64_stream_published_vectors():
+    # SplitMix64 seeded with 0: outputs 1, 2, 3 (Steele, Lea, Flood 2014)
+    assert oracle.splitmix64_at(0, 1) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64_at(0, 2) == 0x6E789E6AA1B965F4
+    assert oracle.splitmix64_at(0, 3) == 0x06C45D188009454F
+
+
+def test_round_priorities_in_range():
+    h = synth.small(seed=2, n=1000, m=3000)
+    ps = np.array([[oracle.round_priority(h, 100.0, r, e) - float(h.weights[e]) for e in range(0, 3000, 7)]
+                   for r in (1, 2, 9)])
+    assert ps.min() >= 0.0 and ps.max() < 100.0 + 1e-3
+    assert abs(ps.mean() - 50.0) < 2.5
+    assert not np.array_equal(ps[0], ps[1])  # redrawn every round
+
+
+def test_tiny_noise_keeps_the_fixed_order():
+    """Noise far below the gaps between (distinct) weights cannot reorder
+    edges: the re-randomised rounds then reproduce the fixed-order run."""
+    rng = np.random.default_rng(4)
+    h = synth.small(seed=4, n=3000, m=9000)
+    h.weights = ((rng.permutation(9000) + 1) / 16384.0).astype(np.float32)  # distinct, gap 2^-14
+    a, b = oracle.match(h), oracle.match(h, noise=2.0 ** -24)
+    assert a.rounds == b.rounds and np.array_equal(a.in_matching, b.in_matching)
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_randomised_definitions(idx):
+    h = [synth.small(seed=6), synth.unweighted(seed=3, n=20_000, m=40_000),
+         synth.large(seed=5, n=20_000, m=40_000, kmax=256), synth.generate(50, 4000, kmin=2, kmax=4, seed=8),
+         synth.generate(300, 2000, kmin=1, kmax=5, seed=9)][idx]
+    r = oracle.match(h, noise=100.0)
+    assert r.status == 0
+    assert oracle.check_disjoint(h, r.in_matching) == -1
+    assert oracle.check_maximal(h, r.in_matching) == -1
+    assert oracle.check_local_max(h, r.in_matching, r.decided_round, noise=100.0) == -1
+    r2 = oracle.match(h, noise=100.0)
+    assert np.array_equal(r.in_matching, r2.in_matching) and r.rounds == r2.rounds
+
+
+def test_randomised_cardinality_bound():
+    """With fresh priorities every round the rounds solve the cardinality
+    problem (Sec. 3.2); the result is maximal, so |M| >= OPT/d (Lemma 1 with
+    unit weights). For the original weights no such bound holds: the local
+    maxima are taken under the noisy priorities."""
+    rng = np.random.default_rng(12)
+    for trial in range(150):
+        h = random_tiny(rng, int(rng.integers(2, 13)), int(rng.integers(1, 15)), int(rng.integers(1, 5)))
+        h.weights = None
+        r = oracle.match(h, noise=float(rng.choice([0.5, 100.0])))
+        d = int(np.max(np.diff(h.eoff)))
+        opt, _ = oracle.brute_opt(h)
+        card = float(r.in_matching.sum())
+        assert opt / d - 1e-9 <= card <= opt + 1e-9
+
+
+def test_randomised_rounds_grow_like_log_m():
+    """Claim 2: with fresh uniform priorities every round, O(log m) rounds."""
+    for m in (1_000, 10_000, 100_000):
+        h = synth.unweighted(seed=1, n=m // 2, m=m)
+        r = oracle.match(h, noise=1.0)
+        assert r.rounds <= 2 * math.log2(m), (m, r.rounds)
+
+
+def test_randomised_mutant_caught():
+    # mutant 6 draws the priorities once instead of before every round
+    h = synth.small(seed=6)
+    r = oracle.match(h, noise=100.0, mutant=6)
+    assert oracle.check_local_max(h, r.in_matching, r.decided_round, noise=100.0) != -1
