@@ -121,6 +121,34 @@ hm_status hm_match(hm_handle *h, void *cuda_stream);
 hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
 
 /*
+ * hm_set_noise - choose the priority rule of the following hm_match and
+ * hm_profile_match calls.
+ *
+ * amplitude == 0 (the default): one fixed strict order for the whole run
+ * (the key defined at hm_create).
+ * amplitude > 0: the paper's re-randomised rounds (Sec. 3.1: random
+ * priorities drawn again before every round; Sec. 5.1). Before round r
+ * (1-based) every live edge e gets
+ *     p_r(e) = base_e + amplitude * U_r(e)          (float32, the product
+ *                                                    and the sum each rounded)
+ *     key_r(e) = (bits(p_r(e)) << 32) | (0xFFFFFFFF - e)
+ * with base_e = weights[e] (1.0f for HM_UNWEIGHTED), U_r(e) = (top 24 bits
+ * of output number (r << 32) + e + 1 of the SplitMix64 generator whose
+ * state starts at the first SplitMix64 output for `seed`) * 2^-24, and e the
+ * input edge id. A vertex's best edge in round r is its live edge of
+ * largest key_r. The result is still unique for a given (input, seed,
+ * amplitude). The 1/d bound of Lemma 1 holds for the cardinality of the
+ * matching (unweighted input) in this mode; with weights plus noise the
+ * matching is locally maximal for the noisy priorities, not for w.
+ * The first match with amplitude > 0 allocates 4*kappa + 16*n + 16*m bytes
+ * more on the device plus 16 bytes per vertex of degree above 2048
+ * (owned by the handle until hm_destroy).
+ * hm_autotune tunes the fixed-order loop and leaves the amplitude set.
+ * Errors: HM_EINVAL (NULL handle, amplitude negative, NaN or infinite).
+ */
+hm_status hm_set_noise(hm_handle *h, float amplitude);
+
+/*
  * hm_launch_config - read and/or set the launch shape of the round kernels
  * (no counterpart in the paper; the result never depends on it).
  *   set  HOST int32[4] or NULL: {kill item size in list entries (64..2^20),

@@ -30,7 +30,7 @@ STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills",
 KERNELS = ("init", "argmax", "win", "kill", "round_end")
 
 # Every entry point of include/hm.h, in declaration order.
-ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_launch_config", "hm_autotune",
+ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_set_noise", "hm_launch_config", "hm_autotune",
                 "hm_result", "hm_result_device",
                 "hm_round_stats", "hm_vertex_state", "hm_profile_match", "hm_create_ms",
                 "hm_probe_random_access", "hm_solve_host", "hm_match_noalloc", "hm_batch_create",
@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "hm_create": ([p, i64, i64, p, p, p, u64, u32, p], i32),
             "hm_match": ([p, p], i32),
             "hm_set_round_cap": ([p, i64], i32),
+            "hm_set_noise": ([p, ctypes.c_float], i32),
             "hm_launch_config": ([p, p, p], i32),
             "hm_autotune": ([p, p, p, p], i32),
             "hm_result": ([p, p, p, p, p], i32),
@@ -175,6 +176,11 @@ class Matcher:
 
     def set_round_cap(self, cap: int) -> None:
         _check(lib().hm_set_round_cap(self.handle, int(cap)))
+
+    def set_noise(self, amplitude: float) -> None:
+        """0: fixed priority order; > 0: priorities re-drawn before every
+        round with this noise amplitude (the paper's randomised rounds)."""
+        _check(lib().hm_set_noise(self.handle, float(amplitude)))
 
     def launch_config(self, config=None) -> tuple:
         """Set (kill_chunk, argmax_bpsm, win_bpsm, kill_bpsm) if given; return the one in force."""

@@ -2,6 +2,7 @@
 #include "hm_internal.cuh"
 
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -170,6 +171,14 @@ hm_status hm_set_round_cap(hm_handle *hh, int64_t cap) {
     return HM_OK;
 }
 
+hm_status hm_set_noise(hm_handle *hh, float amplitude) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return einval("handle is NULL");
+    if (!(amplitude >= 0.f) || std::isinf(amplitude)) return einval("noise amplitude must be finite and >= 0");
+    h->noise = amplitude;
+    return HM_OK;
+}
+
 static hm_status busy_check(Handle *h, cudaStream_t s) {
     if (h->matched_once && s != h->last_stream && cudaEventQuery(h->done) == cudaErrorNotReady)
         return HM_EBUSY;
@@ -187,8 +196,9 @@ hm_status hm_match(hm_handle *hh, void *cuda_stream) {
         g_err = "a match of this handle is still running on another stream";
         return HM_EBUSY;
     }
-    st = launch_match_graph(h, s);
+    st = h->noise > 0.f ? launch_match_graph_rand(h, s) : launch_match_graph(h, s);
     if (st != HM_OK) return st;
+    h->last_random = h->noise > 0.f;
     cudaError_t e = cudaEventRecord(h->done, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     h->last_stream = s;
@@ -210,7 +220,9 @@ hm_status hm_profile_match(hm_handle *hh, void *cuda_stream, double *ms_out, int
     }
     if (!round_ms_out) max_rounds = 0;
     if (max_rounds < 0) return einval("max_rounds < 0");
-    st = profile_match(h, s, ms_out, launches_out, round_ms_out, max_rounds);
+    st = h->noise > 0.f ? profile_match_rand(h, s, ms_out, launches_out, round_ms_out, max_rounds)
+                        : profile_match(h, s, ms_out, launches_out, round_ms_out, max_rounds);
+    h->last_random = h->noise > 0.f;
     h->last_stream = s;
     h->matched_once = true;
     return st;
@@ -251,6 +263,7 @@ hm_status hm_autotune(hm_handle *hh, void *cuda_stream, int32_t *config_out, dou
     double ms = 0;
     st = autotune(h, s, &best, &ms);
     if (st != HM_OK) return st;
+    h->last_random = false;
     cudaEventRecord(h->done, s);
     h->last_stream = s;
     h->matched_once = true;

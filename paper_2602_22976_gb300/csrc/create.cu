@@ -57,14 +57,6 @@ __global__ void k_validate(const int64_t *__restrict__ eoff, const int32_t *__re
     }
 }
 
-// SplitMix64 (Steele, Lea, Flood 2014): first output for a given seed.
-__host__ __device__ inline uint64_t splitmix64_first(uint64_t x) {
-    x += 0x9E3779B97F4A7C15ULL;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
-    return x ^ (x >> 31);
-}
-
 // MurmurHash3 32-bit finaliser (Appleby): a bijection on 32-bit words.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
@@ -188,21 +180,6 @@ __global__ void k_vrec_meta(const int64_t *__restrict__ voff, int64_t n, int4 *_
         const int64_t b = voff[v], e = voff[v + 1];
         vrec[v] = make_int4(-2, 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
     }
-}
-
-template <typename T>
-hm_status dalloc(T **p, uint64_t count, cudaStream_t s, const char *what) {
-    cudaError_t e = cudaMallocAsync((void **)p, (size_t)std::max<uint64_t>(count, 1) * sizeof(T), s);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        char buf[160];
-        snprintf(buf, sizeof buf, "out of device memory allocating %s (%llu bytes)", what,
-                 (unsigned long long)(count * sizeof(T)));
-        set_error(buf);
-        return HM_ENOMEM;
-    }
-    return HM_OK;
 }
 
 template <typename T>

@@ -72,6 +72,7 @@ struct DevState {
     unsigned long long kills;
     unsigned long long winpins;
     unsigned long long proposals;
+    unsigned long long lpack;      // re-randomised rounds: (long lists << 32) | their chunks
 };
 
 struct KillItem {
@@ -110,6 +111,16 @@ struct RoundArgs {
     uint64_t win_cap;      // capacity of win
     cudaGraphConditionalHandle cond;
     int use_cond;
+    // re-randomised rounds only (rrounds.cu)
+    float noise_scale;          // amplitude * 2^-24
+    uint64_t noise_s0;          // SplitMix64 start state of the priority stream
+    int32_t *vadjR;             // vertex lists, compacted in place every round
+    const int2 *ejw;            // j -> {input id, bits of the base priority}
+    const int32_t *jof;         // input id -> j
+    uint32_t *P2;               // second proposal counter buffer
+    int2 *lq;                   // long lists of the round: {vertex, first chunk}
+    unsigned long long *lbest;  // their largest key of the round
+    uint32_t lq_cap;            // capacity of lq / lbest
 };
 
 struct Handle {
@@ -139,6 +150,22 @@ struct Handle {
     unsigned argmax_grid = 0, win_grid = 0, kill_grid = 0;
     LaunchConfig cfg, graph_cfg;
     int32_t *wround = nullptr;
+    // re-randomised rounds (allocated on first use, rrounds.cu)
+    float noise = 0.f;          // 0: fixed order; > 0: amplitude of the per-round noise
+    float graph_noise = 0.f;    // amplitude exec_rand was built with
+    bool last_random = false;   // the last match ran re-randomised rounds
+    int4 *vrecR = nullptr;      // {T[v], 0, list start, live list length}
+    int32_t *vadjR = nullptr;   // vertex lists, compacted in place every round
+    int2 *ejw = nullptr;
+    int32_t *jof = nullptr;
+    uint32_t *P2 = nullptr;
+    int2 *lq = nullptr;
+    unsigned long long *lbest = nullptr;
+    uint32_t lq_cap = 0;
+    unsigned rargmax_grid = 0, rlong_grid = 0;
+    cudaGraphExec_t exec_rand = nullptr;
+    int64_t graph_cap_rand = -1;
+    LaunchConfig graph_cfg_rand;
     int32_t *win = nullptr;
     KillItem *items = nullptr;
     uint8_t *inM = nullptr;
@@ -209,6 +236,49 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
                         int32_t max_rounds);
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);
 void free_handle_buffers(Handle *h);
+// Pieces of the round loop that the re-randomised rounds reuse unchanged.
+void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev);
+// Captures `capture(stream)` into g after the current nodes and returns the
+// one new node nothing depends on (the end of the captured chain).
+hm_status capture_chain(Handle *h, cudaGraph_t g, void (*capture)(Handle *, cudaStream_t, void *), void *ctx,
+                        cudaGraphNode_t *tail);
+// Adds a conditional while node after `after` whose body is `body(stream)`.
+hm_status add_while_loop(Handle *h, cudaGraph_t g, cudaGraphNode_t after, cudaGraphConditionalHandle cond,
+                         void (*body)(Handle *, cudaStream_t, void *), void *ctx);
+
+// ---- re-randomised rounds (rrounds.cu) ----
+// Allocates the extra buffers on first use and builds the j -> input maps.
+hm_status rand_prepare(Handle *h, cudaStream_t s);
+hm_status launch_match_graph_rand(Handle *h, cudaStream_t s);
+hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *launches, double *round_ms,
+                             int32_t max_rounds);
+void free_rand_buffers(Handle *h);
+
+// SplitMix64 (Steele, Lea, Flood 2014): output number k (k >= 1) of the
+// generator whose state starts at s0. The first output for a seed is
+// splitmix64_at(seed, 1).
+__host__ __device__ inline uint64_t splitmix64_at(uint64_t s0, uint64_t k) {
+    uint64_t x = s0 + k * 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+__host__ __device__ inline uint64_t splitmix64_first(uint64_t seed) { return splitmix64_at(seed, 1); }
+
+// Stream-ordered device allocation of `count` elements (at least one);
+// HM_ENOMEM with a message naming `what` on failure.
+template <typename T>
+hm_status dalloc(T **p, uint64_t count, cudaStream_t s, const char *what) {
+    cudaError_t e = cudaMallocAsync((void **)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error(std::string("out of device memory allocating ") + what + " (" +
+                  std::to_string((unsigned long long)(count * sizeof(T))) + " bytes)");
+        return HM_ENOMEM;
+    }
+    return HM_OK;
+}
 
 inline unsigned grid_for(uint64_t work, int threads, int sm_count, int per_sm) {
     uint64_t need = (work + threads - 1) / threads;

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
+        st->lpack = 0;
     }
 }
 
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
     __shared__ uint32_t s_ibase;
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
-    const uint32_t nw = st->nwin;
+    const uint32_t nw = (uint32_t)min((uint64_t)st->nwin, a.win_cap);
     const int t = threadIdx.x;
     unsigned long long kills = 0, winpins = 0;
     for (uint64_t wb = (uint64_t)blockIdx.x * kT; wb < nw; wb += (uint64_t)gridDim.x * kT) {
@@ -473,6 +474,7 @@ __global__ void k_round_end(RoundArgs a) {
     st->nwin = 0;
     st->nitems = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
+    st->lpack = 0;
     if (cont) {
         st->round = r + 1;
         st->parity = par ^ 1;
@@ -513,88 +515,33 @@ unsigned grid_of(const Handle *h, K kernel, int want) {
 void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
     k_argmax<<<h->argmax_grid, kT, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[1], s);
-    k_win<<<h->win_grid, kT, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[2], s);
-    k_kill<<<h->kill_grid, kT, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[3], s);
-    k_round_end<<<1, 32, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[4], s);
+    launch_win_kill_end(h, a, s, ev);
 }
 
 unsigned init_grid(const Handle *h) {
     return grid_for((uint64_t)std::max(h->n, h->m), kT, h->sm_count, 16);
 }
 
-template <typename T>
-hm_status dalloc(T **p, uint64_t count, cudaStream_t s, const char *what) {
-    cudaError_t e = cudaMallocAsync((void **)p, (size_t)std::max<uint64_t>(count, 1) * sizeof(T), s);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        char buf[160];
-        snprintf(buf, sizeof buf, "out of device memory allocating %s (%llu bytes)", what,
-                 (unsigned long long)(count * sizeof(T)));
-        set_error(buf);
-        return HM_ENOMEM;
-    }
-    return HM_OK;
+void capture_init(Handle *h, cudaStream_t s, void *ctx) {
+    k_init<<<init_grid(h), kT, 0, s>>>(*static_cast<const RoundArgs *>(ctx));
+}
+
+void capture_round(Handle *h, cudaStream_t s, void *ctx) {
+    launch_round(h, *static_cast<const RoundArgs *>(ctx), s, nullptr);
 }
 
 hm_status add_match_to_graph_impl(Handle *h, cudaGraph_t g) {
     cudaError_t e;
-    if (!h->cap_stream) {
-        e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-    }
     cudaGraphConditionalHandle cond;
     if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess)
         return cuda_fail(e, "cudaGraphConditionalHandleCreate");
     RoundArgs a = round_args(h);
     a.cond = cond;
     a.use_cond = 1;
-    // init node: captured with no dependencies, found as the one new root
-    size_t before = 0;
-    if ((e = cudaGraphGetNodes(g, nullptr, &before)) != cudaSuccess) return cuda_fail(e, "graph nodes");
-    if ((e = cudaStreamBeginCaptureToGraph(h->cap_stream, g, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return cuda_fail(e, "capture (init)");
-    k_init<<<init_grid(h), kT, 0, h->cap_stream>>>(a);
-    cudaGraph_t out = nullptr;
-    e = cudaStreamEndCapture(h->cap_stream, &out);
-    if (e != cudaSuccess) return cuda_fail(e, "end capture (init)");
-    size_t nn = 0;
-    if ((e = cudaGraphGetNodes(g, nullptr, &nn)) != cudaSuccess || nn != before + 1)
-        return cuda_fail(e == cudaSuccess ? cudaErrorUnknown : e, "graph init node");
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if ((e = cudaGraphGetNodes(g, nodes.data(), &nn)) != cudaSuccess) return cuda_fail(e, "graph nodes");
     cudaGraphNode_t init_node = nullptr;
-    for (cudaGraphNode_t x : nodes) {  // the root that has no dependents yet and is a kernel
-        size_t ndep = 0, nout = 0;
-        cudaGraphNodeGetDependencies(x, nullptr, nullptr, &ndep);
-        cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &nout);
-        cudaGraphNodeType t;
-        cudaGraphNodeGetType(x, &t);
-        if (ndep == 0 && nout == 0 && t == cudaGraphNodeTypeKernel) init_node = x;
-    }
-    if (!init_node) return cuda_fail(cudaErrorUnknown, "graph init node not found");
-    // while node around one round
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t wnode;
-    if ((e = cudaGraphAddNode(&wnode, g, &init_node, nullptr, 1, &cp)) != cudaSuccess)
-        return cuda_fail(e, "cudaGraphAddNode (while)");
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return cuda_fail(e, "capture (round)");
-    launch_round(h, a, h->cap_stream, nullptr);
-    e = cudaStreamEndCapture(h->cap_stream, &out);
-    if (e != cudaSuccess) return cuda_fail(e, "end capture (round)");
-    return HM_OK;
+    hm_status st = capture_chain(h, g, capture_init, &a, &init_node);
+    if (st != HM_OK) return st;
+    return add_while_loop(h, g, init_node, cond, capture_round, &a);
 }
 
 hm_status build_graph(Handle *h) {
@@ -619,6 +566,78 @@ hm_status build_graph(Handle *h) {
 }
 
 }  // namespace
+
+// a2 - a4 of one round (the part both round loops share).
+void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
+    if (ev) cudaEventRecord(ev[1], s);
+    k_win<<<h->win_grid, kT, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[2], s);
+    k_kill<<<h->kill_grid, kT, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[3], s);
+    k_round_end<<<1, 32, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[4], s);
+}
+
+hm_status capture_chain(Handle *h, cudaGraph_t g, void (*capture)(Handle *, cudaStream_t, void *), void *ctx,
+                        cudaGraphNode_t *tail) {
+    cudaError_t e;
+    if (!h->cap_stream) {
+        e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    }
+    size_t before = 0;
+    if ((e = cudaGraphGetNodes(g, nullptr, &before)) != cudaSuccess) return cuda_fail(e, "graph nodes");
+    std::vector<cudaGraphNode_t> old(before);
+    if (before && (e = cudaGraphGetNodes(g, old.data(), &before)) != cudaSuccess)
+        return cuda_fail(e, "graph nodes");
+    std::sort(old.begin(), old.end());
+    // captured with no dependencies: the chain is a new root of g
+    if ((e = cudaStreamBeginCaptureToGraph(h->cap_stream, g, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+    capture(h, h->cap_stream, ctx);
+    cudaGraph_t out = nullptr;
+    if ((e = cudaStreamEndCapture(h->cap_stream, &out)) != cudaSuccess) return cuda_fail(e, "end capture");
+    size_t nn = 0;
+    if ((e = cudaGraphGetNodes(g, nullptr, &nn)) != cudaSuccess) return cuda_fail(e, "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if ((e = cudaGraphGetNodes(g, nodes.data(), &nn)) != cudaSuccess) return cuda_fail(e, "graph nodes");
+    *tail = nullptr;
+    int tails = 0;
+    for (cudaGraphNode_t x : nodes) {
+        if (std::binary_search(old.begin(), old.end(), x)) continue;
+        size_t nout = 0;
+        cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &nout);
+        if (nout == 0) {
+            *tail = x;
+            ++tails;
+        }
+    }
+    if (tails != 1) return cuda_fail(cudaErrorUnknown, "captured chain has no single end node");
+    return HM_OK;
+}
+
+hm_status add_while_loop(Handle *h, cudaGraph_t g, cudaGraphNode_t after, cudaGraphConditionalHandle cond,
+                         void (*body)(Handle *, cudaStream_t, void *), void *ctx) {
+    cudaError_t e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if ((e = cudaGraphAddNode(&wnode, g, &after, nullptr, 1, &cp)) != cudaSuccess)
+        return cuda_fail(e, "cudaGraphAddNode (while)");
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(h->cap_stream, bg, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture (loop body)");
+    body(h, h->cap_stream, ctx);
+    cudaGraph_t out = nullptr;
+    if ((e = cudaStreamEndCapture(h->cap_stream, &out)) != cudaSuccess)
+        return cuda_fail(e, "end capture (loop body)");
+    return HM_OK;
+}
 
 RoundArgs round_args(const Handle *h) {
     RoundArgs a{};
@@ -836,14 +855,15 @@ hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_m
 }
 
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
-    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(h->vrec, h->order, h->n,
-                                                                                out_dev);
+    const int4 *vrec = h->last_random ? h->vrecR : h->vrec;
+    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(vrec, h->order, h->n, out_dev);
     return cudaGetLastError();
 }
 
 // Stream-ordered frees on the handle's own stream: cudaFree would wait for
 // the whole device, stalling every other stream (other handles, requests).
 void free_handle_buffers(Handle *h) {
+    free_rand_buffers(h);
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
                     h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win,
                     h->items, h->inM, h->stats, h->st, h->res_idx, h->res_w, h->res_part};
