@@ -74,6 +74,9 @@ def parse():
                     help="batch workload: skip the one-hm_match-per-instance comparison")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide n and m of the workload (smaller cases for profiler captures)")
+    ap.add_argument("--noise", type=float, default=0.0,
+                    help="> 0: the paper's re-randomised rounds with this noise amplitude "
+                         "(priorities drawn again before every round); 0: fixed order")
     return ap.parse_args()
 
 
@@ -136,15 +139,24 @@ class Clocks:
                 "power_w_max": max(power) if power else None}
 
 
-def kernel_bytes(stats: np.ndarray, n: int, m: int) -> dict:
+def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool = False) -> dict:
     """Algorithmic bytes per kernel kind, summed over rounds (per-unit figures
     in the design doc, section 6), from the per-round counters of hm_round_stats."""
-    ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT = range(8)
-    b = {"init": float(m * (1 + 8 + 4 + 1) + n * (4 + 8)), "argmax": 0.0, "win": 0.0,
-         "kill": 0.0, "round_end": 0.0}
+    ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT, LIVE = range(9)
+    if random:  # flags, two counter buffers, mask; records, offsets; list copy
+        init = float(m * (1 + 4 + 4 + 1) + n * (16 + 16) + kappa * 8)
+    else:
+        init = float(m * (1 + 8 + 4 + 1) + n * (4 + 8))
+    b = {"init": init, "argmax": 0.0, "win": 0.0, "kill": 0.0, "round_end": 0.0}
     for r, row in enumerate(stats):
         row = row.astype(np.float64)
-        if r == 0:  # record read; proposal = P read+write; kept vertex = list write
+        if random:  # list + record; scanned entry = entry + flag; live entry = id/base
+                    # record + compacted write; proposal = record write, id map, offset
+                    # pair, counter read+write, clear of the previous one; kept = list write
+            b["argmax"] += (row[ACT] * ((4 if r else 0) + 16) + row[ADV] * (4 + 1)
+                            + row[LIVE] * (8 + 4) + row[PROP] * (16 + 4 + 16 + 8 + 4)
+                            + row[NEXT] * 4)
+        elif r == 0:  # record read; proposal = P read+write; kept vertex = list write
             b["argmax"] += row[ACT] * 16 + row[PROP] * 8 + row[NEXT] * 4
         else:       # list + record + live flag; skipped entry = entry + flag;
                     # proposal = record write + P read+write; kept vertex = list write
@@ -208,11 +220,11 @@ def run_reference(args, world, rank):
     oracle.build()
     for _ in range(args.warmup):
         for h in hs:
-            oracle.match(h)
+            oracle.match(h, noise=args.noise)
     t0 = time.perf_counter()
     units = 0
     for _ in range(args.steps):
-        units = sum(h.kappa * oracle.match(h).rounds for h in hs)
+        units = sum(h.kappa * oracle.match(h, noise=args.noise).rounds for h in hs)
     dt = time.perf_counter() - t0
     value = units * args.steps / dt
     sample = (f"{hs[0].name}: kappa={hs[0].kappa}, one oracle run per step" if len(hs) == 1 else
@@ -222,7 +234,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
+        "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample,
+                                        "noise": args.noise},
         "cpu_baseline": {"value": value, "unit": "pins/s", "cores": cpu_cores_used(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -400,6 +413,9 @@ def run_ours(args, world, rank, local):
     wl = WORKLOADS[args.workload]
     h = wl["make"](args.seed, args.scale)
     mt = hm.Matcher.from_hypergraph(h)
+    if args.noise > 0:
+        mt.set_noise(args.noise)
+    rnd_mode = args.noise > 0
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -444,7 +460,7 @@ def run_ours(args, world, rank, local):
     prof = mt.profile(stream)
     stats = mt.round_stats()
     create_ms = mt.create_ms()
-    kb = kernel_bytes(stats, h.n, h.m)
+    kb = kernel_bytes(stats, h.n, h.m, h.kappa, rnd_mode)
     dom = max(("argmax", "win", "kill"), key=lambda k: prof[k][0])
     assert all(isinstance(prof[k], tuple) for k in hm.KERNELS)
     peaks = measured_peaks()
@@ -459,13 +475,43 @@ def run_ours(args, world, rank, local):
     kills = float(stats[:, hm.STAT_COLUMNS.index("kills")].sum())
     loop_ms = sum(prof[k][0] for k in hm.KERNELS)
     rounds_run = int(prof["argmax"][1])
-    launches = 1 + 4 * rounds_run  # init + four kernels per round
+    # init + four kernels per round (six in the re-randomised rounds: the argmax
+    # step is three kernels there)
+    launches = 1 + (6 if rnd_mode else 4) * rounds_run
 
     out = {}
     if rank == 0:
         # end to end through hm_solve_host from pinned host memory
         e2e = None
-        if args.e2e_steps > 0:
+        if args.e2e_steps > 0 and rnd_mode:
+            # hm_solve_host runs the fixed order: the public handle calls instead,
+            # from pinned host buffers (copy in, hm_create, hm_set_noise,
+            # hm_match, hm_result to host)
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            eoff_p, pins_p = pin(h.eoff), pin(h.pins)
+            w_p = None if h.weights is None else pin(h.weights)
+
+            def call():
+                d_eoff = eoff_p.to("cuda", non_blocking=True)
+                d_pins = pins_p.to("cuda", non_blocking=True)
+                d_w = None if w_p is None else w_p.to("cuda", non_blocking=True)
+                with hm.Matcher(h.n, h.m, d_eoff, d_pins, d_w, seed=h.seed) as m2:
+                    m2.set_noise(args.noise)
+                    m2.match()
+                    return m2.result()
+            call()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                r2 = call()
+            torch.cuda.synchronize()
+            te = (time.perf_counter() - t0) / args.e2e_steps
+            assert r2.rounds == res.rounds and r2.count == res.count
+            h2d = h.eoff.nbytes + h.pins.nbytes + (0 if h.weights is None else h.weights.nbytes)
+            e2e = {"value": h.kappa * res.rounds / te, "unit": "pins/s", "ms_per_step": te * 1e3,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 4 + 64),
+                   "path": "hm_create + hm_set_noise + hm_match + hm_result"}
+        elif args.e2e_steps > 0:
             pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
             eoff_p, pins_p = pin(h.eoff), pin(h.pins)
             w_p = None if h.weights is None else pin(h.weights)
@@ -492,7 +538,7 @@ def run_ours(args, world, rank, local):
             import oracle
             oracle.build()
             t0 = time.perf_counter()
-            o = oracle.match(h)
+            o = oracle.match(h, noise=args.noise)
             tc = time.perf_counter() - t0
             parity = bool(np.array_equal(o.edges, res.edges) and o.rounds == res.rounds)
             cpu = {"value": h.kappa * o.rounds / tc, "unit": "pins/s", "cores": cpu_cores_used(),
@@ -505,6 +551,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": wl["desc"] + (f" scaled 1/{args.scale}" if args.scale > 1 else ""),
                        "n": h.n, "m": h.m, "kappa": h.kappa,
                        "rounds": res.rounds, "matched": res.count, "weight": res.weight,
+                       "priorities": (f"re-drawn every round, noise amplitude {args.noise}" if rnd_mode
+                                      else "one fixed strict order"),
                        "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps, outside step events",
                        "parallelism": f"replicas x{world}"},
             "time_to_matching_ms": {"mean": t_ms / args.steps, "median": statistics.median(step_ms),

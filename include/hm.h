@@ -199,14 +199,17 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
  * int64[max_rounds][HM_STATS_COLS] receives:
  */
 #define HM_STAT_ACTIVE    0  /* vertices visited by the argmax step */
-#define HM_STAT_ADVANCE   1  /* adjacency entries skipped by the argmax step */
+#define HM_STAT_ADVANCE   1  /* adjacency entries skipped by the argmax step (fixed
+                                order) or scanned by it (re-randomised rounds) */
 #define HM_STAT_PROPOSALS 2  /* vertices that chose a new best edge */
 #define HM_STAT_WINNERS   3  /* edges that joined M */
 #define HM_STAT_WINPINS   4  /* sum of |e| over those edges */
 #define HM_STAT_KILLS     5  /* adjacency entries deactivated by the kill step */
 #define HM_STAT_ITEMS     6  /* kill work items (chunks) */
 #define HM_STAT_NEXT      7  /* vertices kept for the next round */
-#define HM_STATS_COLS     8
+#define HM_STAT_LIVE      8  /* re-randomised rounds: live entries the argmax scan
+                                found; 0 in the fixed order */
+#define HM_STATS_COLS     9
 /* Returns the number of rows written in *rows_out. Errors: HM_EINVAL. */
 hm_status hm_round_stats(hm_handle *h, int64_t *stats, int32_t max_rounds, int32_t *rows_out);
 

@@ -73,6 +73,7 @@ struct DevState {
     unsigned long long winpins;
     unsigned long long proposals;
     unsigned long long lpack;      // re-randomised rounds: (long lists << 32) | their chunks
+    unsigned long long live;       // re-randomised rounds: live entries found by the scan
 };
 
 struct KillItem {

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = 0;
+        st->lpack = st->live = 0;
     }
 }
 
@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
 // Returns 1 if another round must run.
 __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t active, uint32_t nw,
                             uint32_t next, unsigned long long adv, unsigned long long props,
-                            unsigned long long winpins, unsigned long long kills, uint32_t items) {
+                            unsigned long long winpins, unsigned long long kills, uint32_t items,
+                            unsigned long long live) {
     if (r - 1 < kStatRounds) {
         int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
         row[HM_STAT_ACTIVE] = active;
@@ -442,6 +443,7 @@ __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t act
         row[HM_STAT_KILLS] = (int64_t)kills;
         row[HM_STAT_ITEMS] = items;
         row[HM_STAT_NEXT] = next;
+        row[HM_STAT_LIVE] = (int64_t)live;
     }
     int cont = 0;
     if (st->fault) {
@@ -470,11 +472,11 @@ __global__ void k_round_end(RoundArgs a) {
     const uint32_t nw = st->nwin, next = st->cnt[par ^ 1];
     const int64_t active = r == 1 ? a.n : (int64_t)st->cnt[par];
     const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, st->kills,
-                            st->nitems);
+                                  st->nitems, st->live);
     st->nwin = 0;
     st->nitems = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
-    st->lpack = 0;
+    st->lpack = st->live = 0;
     if (cont) {
         st->round = r + 1;
         st->parity = par ^ 1;

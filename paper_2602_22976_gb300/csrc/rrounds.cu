@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = 0;
+        st->lpack = st->live = 0;
     }
 }
 
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
     int32_t *vadj = a.vadjR;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    unsigned long long scanned = 0, props = 0;
+    unsigned long long scanned = 0, props = 0, nlive = 0;
     for (uint32_t g = blockIdx.x * (kT / 32) + wib; g < a.nregions; g += gridDim.x * (kT / 32)) {
         const uint64_t base = (uint64_t)g * a.region;
         uint32_t count;
@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
                     w = propose(a, Pc, nb);
                     keep = true;
                     ++props;
+                    nlive += live;
                 } else {
                     reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurNone, 0);
                 }
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
     }
     block_add_u64(scanned, s_red, &st->adv);
     block_add_u64(props, s_red, &st->proposals);
+    block_add_u64(nlive, s_red, &st->live);
 }
 
 // Chunks of the long lists: one warp per chunk of kChunk entries, maximum
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
     DevState *st = a.st;
     const unsigned long long lp = st->lpack;
     const uint32_t nl = (uint32_t)(lp >> 32), nchunks = (uint32_t)lp;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, nlive = 0;
     if (nl > 0 && nl <= a.lq_cap) {
         const int r = st->round;
         const int lane = threadIdx.x & 31;
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
                 if (__ldg(a.alive + j)) {
                     const unsigned long long k = round_key(a, r, __ldg(a.ejw + j));
                     if (k > mx) mx = k;
+                    ++nlive;
                 }
             }
 #pragma unroll
@@ -308,6 +311,7 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
         }
     }
     block_add_u64(scanned, s_red, &st->adv);
+    block_add_u64(nlive, s_red, &st->live);
 }
 
 // Proposals of the long lists (one thread per list).

@@ -24,6 +24,8 @@ pytestmark = pytest.mark.gpu
 OK, EINVAL, ETIMEOUT = hmlib.HM_OK, hmlib.HM_EINVAL, hmlib.HM_ETIMEOUT
 WIN = hmlib.STAT_COLUMNS.index("winners")
 PROPOSALS = hmlib.STAT_COLUMNS.index("proposals")
+LIVE = hmlib.STAT_COLUMNS.index("live")
+SCANNED = hmlib.STAT_COLUMNS.index("advance")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -53,6 +55,10 @@ def assert_parity(h, noise, res=None, stats=None):
     assert res.rounds == o.rounds
     assert np.array_equal(res.edges, o.edges)
     assert stats[:o.rounds, WIN].tolist() == o.round_stats[:, 2].tolist()
+    # every live entry of every vertex list is seen by the scan: the live
+    # pins of each round, exactly
+    assert stats[:o.rounds, LIVE].tolist() == o.round_stats[:, 1].tolist()
+    assert np.all(stats[:o.rounds, SCANNED] >= stats[:o.rounds, LIVE])
     assert res.weight == oracle.weight(h, o.in_matching)
     return o
 
