@@ -64,6 +64,7 @@ struct DevState {
     uint32_t cnt[2];      // sizes of list0 / list1
     uint32_t nwin;        // winners appended this round
     uint32_t nitems;      // kill items appended this round
+    uint32_t rgrab;       // re-randomised rounds: next region to hand out this round
     int32_t status;       // HM_OK, HM_ETIMEOUT, HM_EINVAL (inconsistent input)
     int32_t rounds_done;  // rounds that started with a live edge
     int32_t finished;     // 1 once the loop has stopped
@@ -115,8 +116,8 @@ struct RoundArgs {
     // re-randomised rounds only (rrounds.cu)
     float noise_scale;          // amplitude * 2^-24
     uint64_t noise_s0;          // SplitMix64 start state of the priority stream
-    int32_t *vadjR;             // vertex lists, compacted in place every round
-    const int2 *ejw;            // j -> {input id, bits of the base priority}
+    const int2 *vadjE;          // vertex lists as {input edge id, bits(base priority)}
+    int2 *vadjR;                // working copy, compacted every round
     const int32_t *jof;         // input id -> j
     uint32_t *P2;               // second proposal counter buffer
     int2 *lq;                   // long lists of the round: {vertex, first chunk}
@@ -156,8 +157,8 @@ struct Handle {
     float graph_noise = 0.f;    // amplitude exec_rand was built with
     bool last_random = false;   // the last match ran re-randomised rounds
     int4 *vrecR = nullptr;      // {T[v], 0, list start, live list length}
-    int32_t *vadjR = nullptr;   // vertex lists, compacted in place every round
-    int2 *ejw = nullptr;
+    int2 *vadjE = nullptr;      // vertex lists as {input edge id, bits(base priority)} (built once)
+    int2 *vadjR = nullptr;      // working copy: short lists rewritten every match, long ones never
     int32_t *jof = nullptr;
     uint32_t *P2 = nullptr;
     int2 *lq = nullptr;
@@ -237,8 +238,10 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
                         int32_t max_rounds);
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);
 void free_handle_buffers(Handle *h);
-// Pieces of the round loop that the re-randomised rounds reuse unchanged.
-void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev);
+// a2 - a4 of one round (shared by both round loops). The kill step reads
+// the edge id of list entry p at a.vadj[p * kill_stride].
+void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev,
+                         int kill_stride = 1);
 // Captures `capture(stream)` into g after the current nodes and returns the
 // one new node nothing depends on (the end of the captured chain).
 hm_status capture_chain(Handle *h, cudaGraph_t g, void (*capture)(Handle *, cudaStream_t, void *), void *ctx,

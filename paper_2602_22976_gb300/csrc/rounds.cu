@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->cnt[0] = st->cnt[1] = 0;
         st->nwin = 0;
         st->nitems = 0;
+        st->rgrab = 0;
         st->status = HM_OK;
         st->rounds_done = 0;
         st->finished = 0;
@@ -397,6 +398,7 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
 // less than half of a random 1-byte store, so the flag is read first and
 // only live targets are written. In round 1 every target is live: plain
 // stores.
+template <int S>  // the edge id of list entry p is vadj[p * S]
 __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
     DevState *st = a.st;
     const uint64_t ni = min((uint64_t)st->nitems, a.item_cap);
@@ -409,10 +411,10 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
     for (uint64_t it = warp; it < ni; it += nwarps) {
         const KillItem x = a.items[it];
         for (int64_t p = x.begin + lane; p < x.end; p += 128) {
-            const int32_t j0 = __ldg(vadj + p);
-            const int32_t j1 = p + 32 < x.end ? __ldg(vadj + p + 32) : -1;
-            const int32_t j2 = p + 64 < x.end ? __ldg(vadj + p + 64) : -1;
-            const int32_t j3 = p + 96 < x.end ? __ldg(vadj + p + 96) : -1;
+            const int32_t j0 = __ldg(vadj + p * S);
+            const int32_t j1 = p + 32 < x.end ? __ldg(vadj + (p + 32) * S) : -1;
+            const int32_t j2 = p + 64 < x.end ? __ldg(vadj + (p + 64) * S) : -1;
+            const int32_t j3 = p + 96 < x.end ? __ldg(vadj + (p + 96) * S) : -1;
             // a stale read can only show 1 for a flag another thread just
             // cleared (flags only go 1 -> 0 here): then it is written twice
             const bool w0 = !check || __ldcg(alive + j0) != 0;
@@ -475,6 +477,7 @@ __global__ void k_round_end(RoundArgs a) {
                                   st->nitems, st->live);
     st->nwin = 0;
     st->nitems = 0;
+    st->rgrab = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
     st->lpack = st->live = 0;
     if (cont) {
@@ -570,11 +573,12 @@ hm_status build_graph(Handle *h) {
 }  // namespace
 
 // a2 - a4 of one round (the part both round loops share).
-void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
+void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int kill_stride) {
     if (ev) cudaEventRecord(ev[1], s);
     k_win<<<h->win_grid, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
-    k_kill<<<h->kill_grid, kT, 0, s>>>(a);
+    if (kill_stride == 2) k_kill<2><<<h->kill_grid, kT, 0, s>>>(a);
+    else k_kill<1><<<h->kill_grid, kT, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     k_round_end<<<1, 32, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[4], s);
@@ -721,7 +725,7 @@ hm_status apply_config(Handle *h, const LaunchConfig &c) {
     h->cfg = c;
     h->argmax_grid = grid_of(h, k_argmax, c.argmax_bpsm);
     h->win_grid = grid_of(h, k_win, c.win_bpsm);
-    h->kill_grid = grid_of(h, k_kill, c.kill_bpsm);
+    h->kill_grid = grid_of(h, k_kill<1>, c.kill_bpsm);
     h->nregions = h->argmax_grid * (kT / 32);
     if (h->nregions > h->regions_cap) h->nregions = h->regions_cap;
     const uint64_t n = (uint64_t)h->n;

@@ -11,16 +11,23 @@
 // With priorities that change every round there is no fixed list order for
 // a cursor to walk. Every round each active vertex scans its live list,
 // takes the largest key among the live entries (Alg. 3's argmax), and
-// compacts the list in place, so an entry is read at most once after its
-// edge died. Lists are scheduled by length:
+// compacts it, so an entry is read at most once after its edge died. List
+// entries carry what the key needs, {input edge id e, bits(base_e)}, so
+// round 1 streams the lists with no random read at all (every edge is live
+// then); later rounds add one 1-byte live-flag read per entry, from an
+// array indexed by input id (m bytes, L2-resident). Round 1 reads the
+// immutable lists (vadjE) and writes the working copy (vadjR); later rounds
+// compact vadjR in place. Lists are scheduled by length:
 //   - at most kLong entries: the 32 vertices of a warp tile are scanned as
-//     one concatenated sequence, 32 entries per step (segmented maximum and
-//     ballot compaction), so short and medium lists keep every lane busy;
+//     one concatenated sequence, kU steps of 32 entries at a time (all their
+//     loads in flight together; segmented maximum and ballot compaction),
+//     so short and medium lists keep every lane busy;
 //   - longer lists: queued with their chunk count (one 64-bit atomic hands
 //     out the queue slot and the first chunk); k_rlong scans the chunks of
 //     kChunk entries with one warp each and combines them per list with a
 //     64-bit atomicMax; k_rfin turns each list's maximum into the vertex's
-//     proposal. Long lists are not compacted.
+//     proposal. Long lists are not compacted: their part of vadjR is
+//     copied once when the handle first runs this mode and never written.
 // Proposals use the P counter of Alg. 1 counted up and double-buffered by
 // round parity: a vertex adds 1 to P_r[T[v]], the edge wins when the count
 // reaches |e|, and the vertex clears the entry it counted in the previous
@@ -30,7 +37,8 @@
 // The win, kill and round-end kernels of the fixed-order loop (rounds.cu)
 // run unchanged on this handle's re-randomised copies of the vertex records
 // and lists: the cursor field stays 0, so the kill range of a matched vertex
-// is its whole (compacted) list.
+// is its whole (compacted) list, and the kill step (reading every second
+// word: the edge ids of the pairs) clears the flags of the input ids there.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -43,6 +51,7 @@ constexpr int kT = 256;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kLong = 2048;   // lists longer than this are scanned in chunks
 constexpr uint32_t kChunk = 2048;  // entries per chunk of a long list
+constexpr int kU = 4;              // 32-entry steps with loads in flight together
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
@@ -75,14 +84,13 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
     __syncthreads();
 }
 
-// key_r(e) of an entry whose ejw record is ew = {e, bits(base_e)}. The
-// product and the sum are rounded separately (no fused multiply-add), as
-// the definition's float32 operations are.
-__device__ __forceinline__ unsigned long long round_key(const RoundArgs &a, int r, int2 ew) {
-    const uint32_t e = (uint32_t)ew.x;
+// key_r(e) of input edge e whose base priority is `base`. The product and
+// the sum are rounded separately (no fused multiply-add), as the
+// definition's float32 operations are.
+__device__ __forceinline__ unsigned long long round_key(const RoundArgs &a, int r, uint32_t e, float base) {
     const uint64_t x = splitmix64_at(a.noise_s0, ((uint64_t)(uint32_t)r << 32) + e + 1u);
     const float u = __uint2float_rn((uint32_t)(x >> 40));
-    const float p = __fadd_rn(__int_as_float(ew.y), __fmul_rn(u, a.noise_scale));
+    const float p = __fadd_rn(base, __fmul_rn(u, a.noise_scale));
     return ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(0xFFFFFFFFu - e);
 }
 
@@ -133,6 +141,7 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         st->cnt[0] = st->cnt[1] = 0;
         st->nwin = 0;
         st->nitems = 0;
+        st->rgrab = 0;
         st->status = HM_OK;
         st->rounds_done = 0;
         st->finished = 0;
@@ -142,10 +151,18 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
     }
 }
 
-// a1 of a re-randomised round for the vertices of the active list (warp g
-// owns region g, as in the fixed-order loop).
-__global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
-    __shared__ unsigned long long s_red[kT / 32];
+// Adds a warp's counter to *dst with one atomic.
+__device__ __forceinline__ void warp_add_u64(unsigned long long x, unsigned long long *dst) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(dst, x);
+}
+
+// a1 of a re-randomised round for the vertices of the active list. The
+// regions are those of the fixed-order loop; warps of a persistent grid
+// take them one at a time from a counter, so that regions with long lists
+// do not leave other warps idle.
+__global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     DevState *st = a.st;
     const int r = st->round;
     const int par = st->parity;
@@ -155,11 +172,16 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
     uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
     uint32_t *Pc = (r & 1) ? a.P2 : a.P;  // counts of this round
     uint32_t *Po = (r & 1) ? a.P : a.P2;  // counts of the previous round
-    int32_t *vadj = a.vadjR;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int2 *src = r == 1 ? a.vadjE : a.vadjR;
+    int2 *dst = a.vadjR;
+    const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     unsigned long long scanned = 0, props = 0, nlive = 0;
-    for (uint32_t g = blockIdx.x * (kT / 32) + wib; g < a.nregions; g += gridDim.x * (kT / 32)) {
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&st->rgrab, 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= a.nregions) break;
         const uint64_t base = (uint64_t)g * a.region;
         uint32_t count;
         if (r == 1) {
@@ -194,49 +216,74 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
             const uint32_t total = __shfl_sync(kFull, inc, 31);
             unsigned long long best = 0;
             uint32_t live = 0;
-            for (uint32_t s0 = 0; s0 < total; s0 += 32) {
-                const uint32_t p = s0 + lane;
-                // owner: the largest lane o with pre_o <= p (it has L_o > 0 when p < total)
-                int o = 0;
+            for (uint32_t s0 = 0; s0 < total; s0 += 32 * kU) {
+                int o[kU];
+                uint32_t opre[kU];
+                int64_t ob[kU];
+                int2 ev[kU];
 #pragma unroll
-                for (int bit = 16; bit; bit >>= 1) {
-                    const uint32_t pc = __shfl_sync(kFull, pre, o + bit);
-                    if (pc <= p) o += bit;
-                }
-                const bool valid = p < total;
-                const uint32_t opre = __shfl_sync(kFull, pre, o);
-                const int64_t ob = (int64_t)(uint32_t)__shfl_sync(kFull, rec.z, o);
-                const int64_t pos = ob + (int64_t)(p - opre);
-                // plain load: this kernel rewrites the list behind the reads
-                const int32_t j = valid ? vadj[pos] : 0;
-                const bool lv = valid && __ldg(a.alive + j) != 0;
-                const unsigned long long key = lv ? round_key(a, r, __ldg(a.ejw + j)) : 0ull;
-                // lanes [sst, lane) of this step hold earlier entries of the same list
-                const uint32_t sst = opre > s0 ? opre - s0 : 0u;
-                const unsigned seg_lt = lt & ~((1u << sst) - 1u);
-                const unsigned lm = __ballot_sync(kFull, lv);
-                const uint32_t carried = __shfl_sync(kFull, live, o);
-                if (lv) vadj[ob + carried + __popc(lm & seg_lt)] = j;  // in-place compaction
-                // segmented running maximum over the step
-                unsigned long long mx = key;
+                for (int u = 0; u < kU; ++u) {
+                    // owner of position p: the largest lane x with pre_x <= p
+                    // (it has L_x > 0 when p < total)
+                    const uint32_t p = s0 + 32 * u + lane;
+                    int x = 0;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const unsigned long long y = __shfl_up_sync(kFull, mx, d);
-                    if (lane >= d && (uint32_t)(lane - d) >= sst && y > mx) mx = y;
+                    for (int bit = 16; bit; bit >>= 1) {
+                        const uint32_t pc = __shfl_sync(kFull, pre, x + bit);
+                        if (pc <= p) x += bit;
+                    }
+                    o[u] = x;
+                    opre[u] = __shfl_sync(kFull, pre, x);
+                    ob[u] = (int64_t)(uint32_t)__shfl_sync(kFull, rec.z, x);
                 }
-                // each owner takes the maximum at the last lane of its piece
-                const bool mine = L > 0 && pre < s0 + 32 && pre + L > s0;
-                const uint32_t tail = mine ? min(pre + L - s0, 32u) - 1u : (uint32_t)lane;
-                const unsigned long long tmx = __shfl_sync(kFull, mx, (int)tail);
-                if (mine) {
-                    if (tmx > best) best = tmx;
-                    const uint32_t lo = pre > s0 ? pre - s0 : 0u;
-                    const unsigned upto = tail == 31u ? kFull : ((2u << tail) - 1u);
-                    live += __popc(lm & upto & ~((1u << lo) - 1u));
+                // plain loads: from round 2 on this kernel rewrites the lists behind the reads
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t p = s0 + 32 * u + lane;
+                    ev[u] = p < total ? src[ob[u] + (int64_t)(p - opre[u])] : make_int2(0, 0);
                 }
-                scanned += valid ? 1u : 0u;
+                bool lvv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t p = s0 + 32 * u + lane;
+                    lvv[u] = p < total && (r == 1 || __ldg(a.alive + ev[u].x) != 0);
+                }
+                __syncwarp();  // every read of this batch precedes its compaction writes
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t su = s0 + 32 * u;
+                    if (su < total) {  // warp-uniform
+                        const bool lv = lvv[u];
+                        const unsigned long long key =
+                            lv ? round_key(a, r, (uint32_t)ev[u].x, __int_as_float(ev[u].y)) : 0ull;
+                        // lanes [sst, lane) of this step hold earlier entries of the same list
+                        const uint32_t sst = opre[u] > su ? opre[u] - su : 0u;
+                        const unsigned seg_lt = lt & ~((1u << sst) - 1u);
+                        const unsigned lm = __ballot_sync(kFull, lv);
+                        const uint32_t carried = __shfl_sync(kFull, live, o[u]);
+                        if (lv) dst[ob[u] + carried + __popc(lm & seg_lt)] = ev[u];  // compaction
+                        // segmented running maximum over the step
+                        unsigned long long mx = key;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const unsigned long long y = __shfl_up_sync(kFull, mx, d);
+                            if (lane >= d && (uint32_t)(lane - d) >= sst && y > mx) mx = y;
+                        }
+                        // each owner takes the maximum at the last lane of its piece
+                        const bool mine = L > 0 && pre < su + 32 && pre + L > su;
+                        const uint32_t tail = mine ? min(pre + L - su, 32u) - 1u : (uint32_t)lane;
+                        const unsigned long long tmx = __shfl_sync(kFull, mx, (int)tail);
+                        if (mine) {
+                            if (tmx > best) best = tmx;
+                            const uint32_t lo = pre > su ? pre - su : 0u;
+                            const unsigned upto = tail == 31u ? kFull : ((2u << tail) - 1u);
+                            live += __popc(lm & upto & ~((1u << lo) - 1u));
+                        }
+                        scanned += su + lane < total ? 1u : 0u;
+                    }
+                }
             }
-            bool keep = lng, w = false;
+            bool keep = false, w = false;
             int32_t nb = -1;
             if (act && !lng) {
                 if (r > 1) Po[rec.x] = 0;  // T[v] of the previous round is what v counted there
@@ -254,6 +301,9 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
             const unsigned km = __ballot_sync(kFull, keep);
             if (keep) out[base + kept + __popc(km & lt)] = v;
             kept += __popc(km);
+            const unsigned lgm = __ballot_sync(kFull, lng);  // long lists stay; k_rfin may drop them
+            if (lng) out[base + kept + __popc(lgm & lt)] = v;
+            kept += __popc(lgm);
             append_winners(a, w, nb);
         }
         if (lane == 0) {
@@ -261,9 +311,9 @@ __global__ void __launch_bounds__(kT) k_rargmax(RoundArgs a) {
             if (kept) atomicAdd(&st->cnt[par ^ 1], kept);
         }
     }
-    block_add_u64(scanned, s_red, &st->adv);
-    block_add_u64(props, s_red, &st->proposals);
-    block_add_u64(nlive, s_red, &st->live);
+    warp_add_u64(scanned, &st->adv);
+    warp_add_u64(props, &st->proposals);
+    warp_add_u64(nlive, &st->live);
 }
 
 // Chunks of the long lists: one warp per chunk of kChunk entries, maximum
@@ -292,9 +342,9 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
             const int64_t e = min(lb + (int64_t)(uint32_t)rec.w, b + (int64_t)kChunk);
             unsigned long long mx = 0;
             for (int64_t p = b + lane; p < e; p += 32) {
-                const int32_t j = __ldg(a.vadjR + p);  // long lists are only read here
-                if (__ldg(a.alive + j)) {
-                    const unsigned long long k = round_key(a, r, __ldg(a.ejw + j));
+                const int2 x = __ldg(a.vadjR + p);  // long lists are only read here
+                if (r == 1 || __ldg(a.alive + x.x)) {
+                    const unsigned long long k = round_key(a, r, (uint32_t)x.x, __int_as_float(x.y));
                     if (k > mx) mx = k;
                     ++nlive;
                 }
@@ -352,13 +402,19 @@ __global__ void __launch_bounds__(kT) k_rfin(RoundArgs a) {
     block_add_u64(props, s_red, &st->proposals);
 }
 
-__global__ void __launch_bounds__(kT) k_ejw(const int32_t *order, const float *w, int64_t m, int2 *ejw,
-                                          int32_t *jof) {
-    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
-        const int32_t e = order[j];
-        ejw[j] = make_int2(e, __float_as_int(w ? w[e] : 1.0f));
-        jof[e] = (int32_t)j;
+// Lists as {input edge id, bits(base priority)} pairs, both copies, and
+// the inverse of the edge order (built once per handle).
+__global__ void __launch_bounds__(kT) k_map(const int32_t *order, const int32_t *vadj, const float *w, int64_t m,
+                                          uint64_t kappa, int2 *vadjE, int2 *vadjR, int32_t *jof) {
+    const uint64_t stride = (uint64_t)gridDim.x * kT;
+    for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += stride) {
+        const int32_t e = __ldg(order + __ldg(vadj + i));
+        const int2 x = make_int2(e, __float_as_int(w ? __ldg(w + e) : 1.0f));
+        vadjE[i] = x;
+        vadjR[i] = x;
     }
+    for (uint64_t j = blockIdx.x * (uint64_t)kT + threadIdx.x; j < (uint64_t)m; j += stride)
+        jof[order[j]] = (int32_t)j;
 }
 
 template <typename K>
@@ -374,11 +430,11 @@ int fit_per_sm(K kernel) {
 RoundArgs rand_args(const Handle *h) {
     RoundArgs a = round_args(h);
     a.vrec = h->vrecR;
-    a.vadj = h->vadjR;
+    a.vadj = reinterpret_cast<const int32_t *>(h->vadjR);  // for the kill step: stride 2
+    a.vadjE = h->vadjE;
     a.vadjR = h->vadjR;
     a.noise_scale = h->noise * (1.0f / 16777216.0f);
     a.noise_s0 = splitmix64_first(h->seed);
-    a.ejw = h->ejw;
     a.jof = h->jof;
     a.P2 = h->P2;
     a.lq = h->lq;
@@ -392,8 +448,6 @@ unsigned rinit_grid(const Handle *h) {
 }
 
 void launch_rinit(const Handle *h, const RoundArgs &a, cudaStream_t s) {
-    if (h->kappa)
-        cudaMemcpyAsync(h->vadjR, h->vadj, (size_t)h->kappa * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     k_rinit<<<rinit_grid(h), kT, 0, s>>>(a);
 }
 
@@ -402,7 +456,7 @@ void launch_rround(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEven
     k_rargmax<<<h->rargmax_grid, kT, 0, s>>>(a);
     k_rlong<<<h->rlong_grid, kT, 0, s>>>(a);
     k_rfin<<<(unsigned)h->sm_count, kT, 0, s>>>(a);
-    launch_win_kill_end(h, a, s, ev);
+    launch_win_kill_end(h, a, s, ev, 2);
 }
 
 void capture_rinit(Handle *h, cudaStream_t s, void *ctx) {
@@ -446,15 +500,15 @@ hm_status build_graph_rand(Handle *h) {
 }  // namespace
 
 hm_status rand_prepare(Handle *h, cudaStream_t s) {
-    h->rargmax_grid = std::max(1u, (h->nregions + kT / 32 - 1) / (kT / 32));
+    h->rargmax_grid = (unsigned)(h->sm_count * fit_per_sm(k_rargmax));
     h->rlong_grid = (unsigned)(h->sm_count * fit_per_sm(k_rlong));
     if (h->vrecR) return HM_OK;
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
     h->lq_cap = (uint32_t)(std::min<uint64_t>(n, h->kappa / kLong) + 1);
     hm_status st;
     if ((st = dalloc(&h->vrecR, n, s, "re-randomised vertex records")) != HM_OK ||
+        (st = dalloc(&h->vadjE, h->kappa, s, "vertex lists in edge ids")) != HM_OK ||
         (st = dalloc(&h->vadjR, h->kappa, s, "re-randomised vertex lists")) != HM_OK ||
-        (st = dalloc(&h->ejw, m, s, "edge ids and base priorities")) != HM_OK ||
         (st = dalloc(&h->jof, m, s, "inverse edge order")) != HM_OK ||
         (st = dalloc(&h->P2, m, s, "second proposal counters")) != HM_OK ||
         (st = dalloc(&h->lq, h->lq_cap, s, "long-list queue")) != HM_OK ||
@@ -463,12 +517,12 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
         return st;
     }
     if (m) {
-        k_ejw<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->weighted ? h->weights : nullptr,
-                                                               h->m, h->ejw, h->jof);
+        k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
+            h->order, h->vadj, h->weighted ? h->weights : nullptr, h->m, h->kappa, h->vadjE, h->vadjR, h->jof);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             free_rand_buffers(h);
-            return cuda_fail(e, "edge id map");
+            return cuda_fail(e, "edge id maps");
         }
     }
     return HM_OK;
@@ -531,12 +585,12 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
 }
 
 void free_rand_buffers(Handle *h) {
-    void *bufs[] = {h->vrecR, h->vadjR, h->ejw, h->jof, h->P2, h->lq, h->lbest};
+    void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->lbest};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, h->cap_stream);
     h->vrecR = nullptr;
+    h->vadjE = nullptr;
     h->vadjR = nullptr;
-    h->ejw = nullptr;
     h->jof = nullptr;
     h->P2 = nullptr;
     h->lq = nullptr;
