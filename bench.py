@@ -89,6 +89,26 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Instance seed of a rank: every replica matches its own hypergraph."""
+    return seed + 1000 * rank
+
+
+def replica_totals(units: float, t_ms: float, world: int, device: str = "cuda") -> tuple:
+    """Whole-job work and time over independent replicas: the units all ranks
+    processed and the slowest rank's time (one SUM and one MAX reduction of
+    two host numbers; nothing on the matching path is exchanged)."""
+    if world <= 1:
+        return units, t_ms
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 class Clocks:
     """nvidia-smi samples every 200 ms while the timed region runs."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -252,11 +272,14 @@ def run_batch(args, world, rank, local):
     import synth
     import paper_2602_22976_gb300 as hm
 
+    import torch.distributed as dist
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hm.build()
     count = max(1, 4096 // args.scale)
     t0 = time.perf_counter()
-    hs = synth.batch(count, seed=args.seed + rank)
+    hs = synth.batch(count, seed=replica_seed(args.seed, rank))
     for h in hs:
         h.seed = args.seed
     t_gen = time.perf_counter() - t0
@@ -272,6 +295,8 @@ def run_batch(args, world, rank, local):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
@@ -280,9 +305,12 @@ def run_batch(args, world, rank, local):
         b.match(stream)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
     step_ms = [x.elapsed_time(y) for x, y in zip(starts, ends)]
     t_ms = float(sum(step_ms))
+    units_all, t_max = replica_totals(units_step * args.steps, t_ms, world)
     ncls, cls, cfg = b.info()
     b.close()
     # plain per-instance launches: one handle and one hm_match per instance
@@ -304,15 +332,15 @@ def run_batch(args, world, rank, local):
             assert rr.rounds == r.rounds and rr.count == r.count
             mt.close()
     out = {
-        "metric": METRIC, "value": units_step * args.steps / (t_ms / 1e3), "unit": "pins/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "metric": METRIC, "value": units_all / (t_max / 1e3), "unit": "pins/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS["batch"]["desc"] + (f" ({count} instances)" if count != 4096 else ""),
                    "instances": count, "sum_kappa": int(sum(h.kappa for h in hs)),
                    "sum_n": int(sum(h.n for h in hs)), "size_classes": int(ncls),
                    "class_launch_configs": cfg.tolist(), "l2": "inputs larger than L2"},
-        "instances_per_s": count * args.steps / (t_ms / 1e3),
+        "instances_per_s": count * world * args.steps / (t_max / 1e3),
         "time_to_matching_ms": {"median": statistics.median(step_ms)},
         "create_s": t_create, "generate_s": t_gen,
         "plain_per_instance": None if plain_ms is None else {
@@ -322,6 +350,9 @@ def run_batch(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 # ------------------------------------------------------------------ serving arm
@@ -333,12 +364,16 @@ def run_serve(args, world, rank, local):
     import synth
     import paper_2602_22976_gb300 as hm
 
+    import torch.distributed as dist
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hm.build()
-    rng = np.random.default_rng(args.seed)
+    seed = replica_seed(args.seed, rank)
+    rng = np.random.default_rng(seed)
     pool_n = max(8, 128 // args.scale)
     kap = np.exp(rng.uniform(np.log(1e3), np.log(1e7 / args.scale), size=pool_n)).astype(np.int64)
-    pool = [synth.serve_request(int(k), seed=args.seed * 100_000 + i) for i, k in enumerate(kap)]
+    pool = [synth.serve_request(int(k), seed=seed * 100_000 + i) for i, k in enumerate(kap)]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     arrays = [(pin(h.eoff), pin(h.pins), pin(h.weights)) for h in pool]
     units = []  # kappa * rounds of every pool request (from a solo run)
@@ -365,7 +400,7 @@ def run_serve(args, world, rank, local):
         work = float(sum(units[k] for k, _ in tickets))
         return {"rate_req_s": rate, "requests": count, "slots": slots,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "pins_per_s": work / wall, "req_per_s": count / wall,
+                "pins_per_s": work / wall, "req_per_s": count / wall, "work": work, "wall_s": wall,
                 "peak_inflight": st["peak_inflight"], "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9}
 
     slots = 8
@@ -377,10 +412,13 @@ def run_serve(args, world, rank, local):
         sweep.append(run(rate, max(count, 16), slots))
     clk = clocks.stop()
     # saturated throughput: the whole pool at once, served vs one request at a time
+    if world > 1:
+        dist.barrier()
     served = run(1e9, 2 * pool_n, slots)
+    work_all, wall_max = replica_totals(served["work"], served["wall_s"] * 1e3, world)
     serial = run(1e9, 2 * pool_n, 1)
     out = {
-        "metric": METRIC, "value": served["pins_per_s"], "unit": "pins/s", "n_gpus": world,
+        "metric": METRIC, "value": work_all / (wall_max / 1e3), "unit": "pins/s", "n_gpus": world,
         "steps": 2 * pool_n, "warmup": 0, "ms_per_step": 1e3 / served["req_per_s"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
@@ -396,6 +434,9 @@ def run_serve(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 # ------------------------------------------------------------------ our arm
@@ -411,7 +452,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hm.build()
     wl = WORKLOADS[args.workload]
-    h = wl["make"](args.seed, args.scale)
+    h = wl["make"](replica_seed(args.seed, rank), args.scale)
     mt = hm.Matcher.from_hypergraph(h)
     if args.noise > 0:
         mt.set_noise(args.noise)
@@ -445,15 +486,7 @@ def run_ours(args, world, rank, local):
     t_ms = float(sum(step_ms))
     res2 = mt.result()
     assert res2.rounds == res.rounds and res2.count == res.count
-    units = float(h.kappa) * res.rounds * args.steps
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([units, t_ms], dtype=torch.float64, device="cuda")
-        u = tt[0:1].clone()
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tm = tt[1:2].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        units, t_max = float(u.item()), float(tm.item())
+    units, t_max = replica_totals(float(h.kappa) * res.rounds * args.steps, t_ms, world)
     value = units / (t_max / 1e3)
 
     # per-kernel replay for the roofline
