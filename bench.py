@@ -189,27 +189,41 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
     return b
 
 
-def kernel_source_hash() -> str:
-    """Hash of the round kernels' source: a stored ncu traffic figure is only
+# kernel step of the bench line -> (row name in profiles/traffic.md, its source file)
+TRAFFIC_ROWS = {
+    ("argmax", False): ("k_argmax", "rounds.cu"),
+    ("win", False): ("k_win", "rounds.cu"),
+    ("kill", False): ("k_kill", "rounds.cu"),
+    ("argmax", True): ("k_rargmax+k_rlong+k_rfin", "rrounds.cu"),
+    ("win", True): ("k_win", "rounds.cu"),
+    ("kill", True): ("k_kill", "rounds.cu"),
+}
+
+
+def kernel_source_hash(source: str = "rounds.cu") -> str:
+    """Hash of a kernel source file: a stored ncu traffic figure is only
     valid for the kernel version it was measured on."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2602_22976_gb300", "csrc", "rounds.cu")
+    p = os.path.join(ROOT, "paper_2602_22976_gb300", "csrc", source)
     with open(p, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(kernel: str) -> float | None:
-    """Per-launch DRAM bytes of `kernel` at the full bench size, read from the
-    committed ncu summary (profiles/traffic.md) when it matches this source."""
+def measured_traffic(step: str, randomised: bool) -> float | None:
+    """Per-launch DRAM bytes of a kernel step at the full bench size, read from
+    the committed ncu summary (profiles/traffic.md) when the row was measured
+    on this source and in this mode (fixed order / re-randomised rounds)."""
     p = os.path.join(ROOT, "profiles", "traffic.md")
+    row, source = TRAFFIC_ROWS[(step, randomised)]
     if not os.path.exists(p):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(source)
+    mode = "re-randomised" if randomised else "fixed"
     for line in open(p):
         parts = [x.strip() for x in line.strip().strip("|").split("|")]
-        if len(parts) >= 3 and parts[0] == kernel and parts[1] == want:
+        if len(parts) >= 4 and parts[0] == row and parts[1] == mode and parts[2] == want:
             try:
-                return float(parts[2])
+                return float(parts[3])
             except ValueError:
                 return None
     return None
@@ -592,9 +606,9 @@ def run_ours(args, world, rank, local):
                                     "p99": float(np.percentile(step_ms, 99))},
             "create_ms": create_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom),
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, rnd_mode),
                          "alg_bytes_per_launch": kb[dom] / max(1, prof[dom][1]),
-                         "kernel_source": kernel_source_hash(),
+                         "kernel_source": kernel_source_hash(TRAFFIC_ROWS[(dom, rnd_mode)][1]),
                          "peak_source": peaks["source"],
                          "loop_gbs": total_bytes / (loop_ms / 1e3) / 1e9},
             "random_access": {
