@@ -170,22 +170,26 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
     b = {"init": init, "argmax": 0.0, "win": 0.0, "kill": 0.0, "round_end": 0.0}
     for r, row in enumerate(stats):
         row = row.astype(np.float64)
+        # winner: offset pair, order, mask, round; winner pin: pin, record read + write;
+        # kill range: item write
+        winb = row[WIN] * (16 + 4 + 1 + 4) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 8
         if random:  # list + record; scanned entry = entry + flag; live entry = id/base
                     # record + compacted write; proposal = record write, id map, offset
                     # pair, counter read+write, clear of the previous one; kept = list write
             b["argmax"] += (row[ACT] * ((4 if r else 0) + 16) + row[ADV] * (4 + 1)
                             + row[LIVE] * (8 + 4) + row[PROP] * (16 + 4 + 16 + 8 + 4)
                             + row[NEXT] * 4)
-        elif r == 0:  # record read; proposal = P read+write; kept vertex = list write
-            b["argmax"] += row[ACT] * 16 + row[PROP] * 8 + row[NEXT] * 4
-        else:       # list + record + live flag; skipped entry = entry + flag;
-                    # proposal = record write + P read+write; kept vertex = list write
-            b["argmax"] += (row[ACT] * (4 + 16 + 1) + row[ADV] * (4 + 1)
-                            + row[PROP] * (8 + 8) + row[NEXT] * 4)
-        # winner: list, offset pair, order, mask; winner pin: pin, record read+write; item write
-        b["win"] += row[WIN] * (4 + 16 + 4 + 1) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 16
-        # item read; killed entry: entry + flag write
-        b["kill"] += row[ITEM] * 16 + row[KILL] * (4 + 1)
+        else:
+            if r == 0:  # record read; proposal = P read+write; kept vertex = list write
+                b["argmax"] += row[ACT] * 16 + row[PROP] * 8 + row[NEXT] * 4
+            else:       # list + record + live flag; skipped entry = entry + flag;
+                        # proposal = record write + P read+write; kept vertex = list write
+                b["argmax"] += (row[ACT] * (4 + 16 + 1) + row[ADV] * (4 + 1)
+                                + row[PROP] * (8 + 8) + row[NEXT] * 4)
+            b["argmax"] += row[WIN] * (4 + 4 + 4)  # winner staged, read, listed
+        b["win"] += winb + row[WIN] * 4  # the winner list
+        # kill range read; killed entry: entry + flag
+        b["kill"] += row[ITEM] * 8 + row[KILL] * (4 + 1)
     return b
 
 
@@ -522,9 +526,9 @@ def run_ours(args, world, rank, local):
     kills = float(stats[:, hm.STAT_COLUMNS.index("kills")].sum())
     loop_ms = sum(prof[k][0] for k in hm.KERNELS)
     rounds_run = int(prof["argmax"][1])
-    # init + four kernels per round (six in the re-randomised rounds: the argmax
-    # step is three kernels there)
-    launches = 1 + (6 if rnd_mode else 4) * rounds_run
+    # init + three kernels per round (argmax, win, kill with the round end);
+    # five in the re-randomised rounds (the argmax step is three kernels there)
+    launches = 1 + (5 if rnd_mode else 3) * rounds_run
 
     out = {}
     if rank == 0:

@@ -151,9 +151,10 @@ hm_status hm_set_noise(hm_handle *h, float amplitude);
 /*
  * hm_launch_config - read and/or set the launch shape of the round kernels
  * (no counterpart in the paper; the result never depends on it).
- *   set  HOST int32[4] or NULL: {kill item size in list entries (64..2^20),
- *        blocks per SM of the argmax, win and kill kernels (0 = as many as
- *        fit)}; takes effect at the next hm_match
+ *   set  HOST int32[4] or NULL: {least list entries one warp of the kill
+ *        kernel takes (64..2^20), blocks per SM of the argmax, win and kill
+ *        kernels (0 = as many as fit; the win kernel runs only in the
+ *        re-randomised rounds)}; takes effect at the next hm_match
  *   get  HOST int32[4] or NULL: the config in force
  * Errors: HM_EINVAL.
  */
@@ -205,7 +206,7 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
 #define HM_STAT_WINNERS   3  /* edges that joined M */
 #define HM_STAT_WINPINS   4  /* sum of |e| over those edges */
 #define HM_STAT_KILLS     5  /* adjacency entries deactivated by the kill step */
-#define HM_STAT_ITEMS     6  /* kill work items (chunks) */
+#define HM_STAT_ITEMS     6  /* kill ranges (one per newly matched vertex) */
 #define HM_STAT_NEXT      7  /* vertices kept for the next round */
 #define HM_STAT_LIVE      8  /* re-randomised rounds: live entries the argmax scan
                                 found; 0 in the fixed order */
@@ -237,10 +238,13 @@ hm_status hm_vertex_state(hm_handle *h, int32_t *best_edge_out);
  * kernel; hm_match is the production path. Errors: as hm_match.
  */
 #define HM_K_INIT    0  /* per-match state reset */
-#define HM_K_ARGMAX  1  /* a1: vertex argmax (cursor advance) + proposals */
-#define HM_K_WIN     2  /* a2: winners join M, their vertices are marked */
-#define HM_K_KILL    3  /* a3: deactivate edges of newly matched vertices */
-#define HM_K_ROUND   4  /* a4: round bookkeeping, termination test */
+#define HM_K_ARGMAX  1  /* a1: vertex argmax (cursor advance) + proposals; in the
+                           fixed order also a2 (one kernel) */
+#define HM_K_WIN     2  /* a2: winners join M, their vertices are marked (its own
+                           kernel only in the re-randomised rounds) */
+#define HM_K_KILL    3  /* a3: deactivate edges of newly matched vertices, and a4 */
+#define HM_K_ROUND   4  /* a4: round bookkeeping, termination test: part of the
+                           kill kernel, so no launches and no time of its own */
 #define HM_K_COUNT   5
 hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int64_t *launches_out,
                            double *round_ms_out, int32_t max_rounds);

@@ -24,8 +24,13 @@
 //                       place, with its length in lcnt[parity][g]
 //   lcnt   uint32[2][nregions] region lengths
 //   wstage int32[nregions*region] per-region staging of a round's winners
-//   win    int32[min(m,n)] winners of the current round, contiguous
-//   items  KillItem[n + kappa/kMinKillChunk + 1] kill ranges of the current round
+//   win    int32[min(m,n)] winners of the current round, contiguous (the
+//                       re-randomised rounds; the fixed order handles its
+//                       winners inside the argmax kernel)
+//   items  KillItem[n+1] kill ranges of the current round: one per newly
+//                       matched vertex, {first list entry, offset of the
+//                       range in the round's concatenation of all ranges},
+//                       the offsets ascending with the item index
 //   wround int32[m]     round in which an edge joined M (input numbering; only
 //                       read for matched edges)
 //   inM    uint8[m]     result mask, input numbering
@@ -42,11 +47,11 @@ namespace hm {
 
 constexpr int32_t kCurMatched = -1;  // vertex covered by the matching
 constexpr int32_t kCurNone = -2;     // vertex has no live edge (or degree 0)
-constexpr int kMinKillChunk = 64;    // smallest kill item size a launch config may use
+constexpr int kMinKillChunk = 64;    // smallest kill slice (entries per warp) a launch config may use
 
 // Launch shape of the round kernels; the autotuner picks it per handle.
 struct LaunchConfig {
-    int kill_chunk = 256;  // max list entries per kill item
+    int kill_chunk = 256;  // least list entries a warp of the kill step takes
     int argmax_bpsm = 0;   // blocks per SM of k_argmax (0 = all that fit)
     int win_bpsm = 0;      // blocks per SM of k_win
     int kill_bpsm = 0;     // blocks per SM of k_kill
@@ -62,8 +67,8 @@ struct DevState {
     int32_t round;        // current round, 1-based
     int32_t parity;       // list index read by the current round
     uint32_t cnt[2];      // sizes of list0 / list1
-    uint32_t nwin;        // winners appended this round
-    uint32_t nitems;      // kill items appended this round
+    uint32_t nwin;        // winners of this round
+    uint32_t kdone;       // blocks of the kill step that have finished
     uint32_t rgrab;       // re-randomised rounds: next region to hand out this round
     int32_t status;       // HM_OK, HM_ETIMEOUT, HM_EINVAL (inconsistent input)
     int32_t rounds_done;  // rounds that started with a live edge
@@ -75,11 +80,15 @@ struct DevState {
     unsigned long long proposals;
     unsigned long long lpack;      // re-randomised rounds: (long lists << 32) | their chunks
     unsigned long long live;       // re-randomised rounds: live entries found by the scan
+    unsigned long long kpack;      // kill ranges of the round: (entries << 32) | items
 };
 
+// One kill range: list entries [begin, begin + length) where length is the
+// next item's ebase (or the round's total) minus this ebase. kappa < 2^32,
+// so both fit 32 bits.
 struct KillItem {
-    int64_t begin;
-    int64_t end;
+    uint32_t begin;
+    uint32_t ebase;
 };
 
 // Everything a round kernel touches; passed by value.
@@ -238,8 +247,10 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
                         int32_t max_rounds);
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);
 void free_handle_buffers(Handle *h);
-// a2 - a4 of one round (shared by both round loops). The kill step reads
-// the edge id of list entry p at a.vadj[p * kill_stride].
+// a2 - a4 of one round for a loop whose argmax step leaves the winners in
+// a.win (the re-randomised rounds): win kernel, then the kill kernel, which
+// also ends the round. The kill step reads the edge id of list entry p at
+// a.vadj[p * kill_stride]. ev (or null): events 1-4 of a profiled round.
 void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev,
                          int kill_stride = 1);
 // Captures `capture(stream)` into g after the current nodes and returns the

@@ -1,7 +1,7 @@
 // rounds.cu - the round loop of locally-maximal hypergraph matching
 // (Sec. 3.1, Alg. 1, Alg. 3) on the device.
 //
-// One round is four kernels:
+// One round is three kernels:
 //   k_argmax    a1: every active vertex v makes T[v] the highest-priority
 //               live edge of its list. The list is sorted by decreasing
 //               priority and edges only ever die, so T[v] is a cursor that
@@ -10,15 +10,18 @@
 //               vertex counts down P[e]; the vertex that brings P[e] to 0 has
 //               seen e chosen by all |e| of its vertices (the test P[e] = |e|
 //               of Alg. 1, Sec. 4.1) and appends e to the winners.
-//   k_win       a2: winners join M; their vertices become matched and emit
-//               their remaining adjacency (from the cursor on) as kill ranges.
-//   k_kill      a3: every edge in a kill range is deactivated (the vertex-side
-//               deactivation of Alg. 1; the writes race benignly, Sec. 4.2).
-//   k_round_end a4: counters, termination test, next active list, and the
+//   k_win       a2: winners join M; their vertices become matched and each
+//               emits the rest of its list (from its cursor on) as one kill
+//               range.
+//   k_kill      a3 + a4: every entry of every kill range is deactivated (the
+//               vertex-side deactivation of Alg. 1; the writes race benignly,
+//               Sec. 4.2). The ranges are read as one concatenated sequence
+//               split evenly over the warps. The block that finishes last
+//               ends the round: counters, termination test, and the
 //               conditional of the CUDA graph's while node.
 // The active vertex list is compacted inside k_argmax (vertices that are
-// matched or have no live edge left drop out) with one block scan and one
-// counter atomic per 1024 list entries.
+// matched or have no live edge left drop out), each warp in place in its own
+// region of the list.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -46,44 +49,6 @@ __device__ __forceinline__ T warp_inclusive_scan(T x) {
         const T y = __shfl_up_sync(kFull, x, d);
         if (lane >= d) x += y;
     }
-    return x;
-}
-
-// Exclusive scan over a block of NT threads (one value each); *total gets
-// the block sum. s_warp: NT/32 + 1 words of shared memory. Ends with a
-// barrier, so s_warp may be reused right away.
-template <int NT = kT>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t inc = warp_inclusive_scan(x);
-    if (lane == 31) s_warp[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        const uint32_t t = lane < NT / 32 ? s_warp[lane] : 0u;
-        const uint32_t ti = warp_inclusive_scan(t);
-        if (lane < NT / 32) s_warp[lane] = ti - t;
-        if (lane == NT / 32 - 1) s_warp[NT / 32] = ti;
-    }
-    __syncthreads();
-    const uint32_t r = s_warp[wid] + inc - x;
-    *total = s_warp[NT / 32];
-    __syncthreads();
-    return r;
-}
-
-// Largest i in [0, hi] with pre[i] <= k (pre ascending, pre[0] == 0 <= k).
-__device__ __forceinline__ int last_le(const uint32_t *pre, int hi, uint32_t k) {
-    int lo = 0;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
     return x;
 }
 
@@ -119,14 +84,14 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->parity = 0;
         st->cnt[0] = st->cnt[1] = 0;
         st->nwin = 0;
-        st->nitems = 0;
+        st->kdone = 0;
         st->rgrab = 0;
         st->status = HM_OK;
         st->rounds_done = 0;
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = st->live = 0;
+        st->lpack = st->live = st->kpack = 0;
     }
 }
 
@@ -230,14 +195,81 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
     return keep;
 }
 
-// a1: argmax (cursor advance) + proposals + win test + list compaction.
+// a2 for up to 32 winners, one per lane (j = relabelled edge id, or -1):
+// the edge joins M (input numbering, with its round), every vertex of it is
+// marked matched, and each vertex emits one kill range: its list from the
+// cursor on (the winner's own entry included, which kills the winner). The
+// pins of the warp's winners are spread over the lanes 32 at a time; items
+// and their entries are reserved with one 64-bit atomic per 32 pins, so the
+// item order and the entry offsets ascend together. All 32 lanes must call.
+__device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, unsigned long long &winpins) {
+    const int lane = threadIdx.x & 31;
+    uint32_t len = 0;
+    int64_t b = 0;
+    if (j >= 0) {
+        b = __ldg(a.eoffj + j);
+        len = (uint32_t)(__ldg(a.eoffj + j + 1) - b);
+        const int32_t ein = __ldg(a.order + j);
+        a.inM[ein] = 1;
+        a.wround[ein] = r;
+        winpins += len;
+    }
+    const uint32_t inc = warp_inclusive_scan(len);
+    const uint32_t exc = inc - len;
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
+    const unsigned lt = lanemask_lt();
+    for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+        const uint32_t q = p0 + lane;
+        // owner of pin q: the largest lane k with exc_k <= q (exc ascends)
+        int k = 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const uint32_t e = __shfl_sync(kFull, exc, k + d);
+            if (e <= q) k += d;
+        }
+        const int32_t jk = __shfl_sync(kFull, j, k);
+        const int64_t bk = __shfl_sync(kFull, b, k);
+        const uint32_t ek = __shfl_sync(kFull, exc, k);
+        uint32_t ibeg = 0, ilen = 0;
+        if (q < total) {
+            const int32_t v = __ldg(a.pinsj + bk + (q - ek));
+            const int4 rec = a.vrec[v];
+            const uint32_t c = (uint32_t)rec.z + (uint32_t)rec.y;
+            const uint32_t end = (uint32_t)rec.z + (uint32_t)rec.w;
+            // T[v] must be the winner: v chose it, and nothing moves it
+            if (rec.x == jk && c < end) {
+                reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurMatched, 0);
+                ibeg = c;
+                ilen = end - c;
+            } else {
+                a.st->fault = 1;
+            }
+        }
+        const unsigned has = __ballot_sync(kFull, ilen > 0);
+        const uint32_t iinc = warp_inclusive_scan(ilen);
+        const uint32_t itot = __shfl_sync(kFull, iinc, 31);
+        unsigned long long old = 0;
+        if (lane == 0 && has)
+            old = atomicAdd(&a.st->kpack, ((unsigned long long)itot << 32) | (unsigned long long)__popc(has));
+        old = __shfl_sync(kFull, old, 0);
+        if (ilen) {
+            const uint64_t idx = (uint64_t)(uint32_t)old + (uint32_t)__popc(has & lt);
+            if (idx < a.item_cap) a.items[idx] = KillItem{ibeg, (uint32_t)(old >> 32) + iinc - ilen};
+            else a.st->fault = 2;
+        }
+    }
+}
+
+// a1: argmax (cursor advance), proposals, win test, list compaction.
 // Warp g owns region g of the active list (the active vertices of one
 // vertex range) and compacts it in place into the other list with ballots:
 // no barrier and no shared counter inside the loop, so a lane that walks a
 // long run of dead entries only holds up its own warp. T[v] is kept as an
-// edge id, so the common case - T[v] still live - costs one state read and
+// edge id, so the common case - T[v] still live - costs one record read and
 // one flag read. At the end each block reserves one slot range for its
-// warps' winners and copies them into the contiguous winner list.
+// warps' winners and copies them into the contiguous winner list (k_win
+// reads the winners' vertex records, which must be complete: that is what
+// keeps a2 in its own kernel).
 __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     __shared__ uint32_t s_keep[kT / 32], s_won[kT / 32];
@@ -301,132 +333,31 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
     }
     __syncthreads();
     if (g < a.nregions)
-        for (uint32_t i = lane; i < won; i += 32)
-            a.win[s_wbase + s_won[wib] + i] = a.wstage[(uint64_t)g * a.region + i];
+        for (uint32_t i = lane; i < won; i += 32) {
+            const uint64_t idx = (uint64_t)s_wbase + s_won[wib] + i;
+            if (idx < a.win_cap) a.win[idx] = a.wstage[(uint64_t)g * a.region + i];
+            else st->fault = 2;
+        }
     block_add_u64(adv, s_red, &st->adv);
     block_add_u64(props, s_red, &st->proposals);
 }
 
-// a2: winners join M; every vertex of a winner is marked matched and emits
-// its list from the cursor on as kill items of <= kill_chunk entries.
-// Blocks take kT winners at a time and spread their pins evenly over the
-// threads (prefix sum of edge sizes + binary search); item slots are
-// reserved with one atomic per kT pins and written by the whole block.
+// a2: each warp takes 32 winners of the round at a time (warp_win). The
+// winners' vertex records were completed by the argmax kernel.
 __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
-    __shared__ int64_t s_wbeg[kT];
-    __shared__ int32_t s_wj[kT];
-    __shared__ uint32_t s_wpre[kT + 1];
-    __shared__ int64_t s_c[kT], s_end[kT];
-    __shared__ uint32_t s_ipre[kT + 1];
-    __shared__ uint32_t s_warp[kT / 32 + 1];
-    __shared__ uint32_t s_ibase;
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
     const uint32_t nw = (uint32_t)min((uint64_t)st->nwin, a.win_cap);
-    const int t = threadIdx.x;
-    unsigned long long kills = 0, winpins = 0;
-    for (uint64_t wb = (uint64_t)blockIdx.x * kT; wb < nw; wb += (uint64_t)gridDim.x * kT) {
-        uint32_t len = 0;
-        if (wb + t < nw) {
-            const int32_t j = a.win[wb + t];
-            const int64_t b = a.eoffj[j], e = a.eoffj[j + 1];
-            s_wbeg[t] = b;
-            s_wj[t] = j;
-            len = (uint32_t)(e - b);
-            const int32_t ein = a.order[j];
-            a.inM[ein] = 1;
-            a.wround[ein] = st->round;
-            winpins += len;
-        }
-        uint32_t npins;
-        s_wpre[t] = block_exclusive_scan(len, s_warp, &npins);
-        if (t == 0) s_wpre[kT] = npins;
-        __syncthreads();
-        for (uint32_t p0 = 0; p0 < npins; p0 += kT) {
-            const uint32_t q = p0 + t;
-            uint32_t nch = 0;
-            int64_t c = 0, end = 0;
-            if (q < npins) {
-                const int w = last_le(s_wpre, kT - 1, q);
-                const int32_t v = __ldg(a.pinsj + s_wbeg[w] + (q - s_wpre[w]));
-                const int4 rec = a.vrec[v];
-                c = (int64_t)(uint32_t)rec.z + rec.y;
-                end = (int64_t)(uint32_t)rec.z + (int64_t)(uint32_t)rec.w;
-                // T[v] must be the winner: v chose it, and nothing moves it
-                if (rec.x == s_wj[w] && c < end) {
-                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurMatched, 0);
-                    nch = (uint32_t)((end - c + a.kill_chunk - 1) / a.kill_chunk);
-                    kills += (unsigned long long)(end - c);
-                } else {
-                    st->fault = 1;
-                }
-            }
-            s_c[t] = c;
-            s_end[t] = end;
-            uint32_t nitems;
-            s_ipre[t] = block_exclusive_scan(nch, s_warp, &nitems);
-            if (t == 0) {
-                s_ipre[kT] = nitems;
-                uint32_t b = nitems ? atomicAdd(&st->nitems, nitems) : 0u;
-                if ((uint64_t)b + nitems > a.item_cap) {
-                    st->fault = 2;
-                    b = 0xFFFFFFFFu;
-                }
-                s_ibase = b;
-            }
-            __syncthreads();
-            const uint32_t ib = s_ibase;
-            if (ib != 0xFFFFFFFFu) {
-                for (uint32_t x = t; x < nitems; x += kT) {
-                    const int pi = last_le(s_ipre, kT - 1, x);
-                    const int64_t lo = s_c[pi] + (int64_t)(x - s_ipre[pi]) * a.kill_chunk;
-                    const int64_t hi = lo + a.kill_chunk < s_end[pi] ? lo + a.kill_chunk : s_end[pi];
-                    a.items[(uint64_t)ib + x] = KillItem{lo, hi};
-                }
-            }
-            __syncthreads();
-        }
-    }
-    block_add_u64(kills, s_red, &st->kills);
-    block_add_u64(winpins, s_red, &st->winpins);
-}
-
-// a3: deactivate every entry of every kill item. A warp takes one item
-// (<= kill_chunk entries) at a time; each lane has four entries in flight.
-// From round 2 on most targets are already dead (they sit behind the
-// cursors of other vertices), and on this GPU a random 1-byte load costs
-// less than half of a random 1-byte store, so the flag is read first and
-// only live targets are written. In round 1 every target is live: plain
-// stores.
-template <int S>  // the edge id of list entry p is vadj[p * S]
-__global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
-    DevState *st = a.st;
-    const uint64_t ni = min((uint64_t)st->nitems, a.item_cap);
-    const bool check = st->round > 1;
+    const int r = st->round;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
-    const int32_t *__restrict__ vadj = a.vadj;
-    uint8_t *__restrict__ alive = a.alive;
-    for (uint64_t it = warp; it < ni; it += nwarps) {
-        const KillItem x = a.items[it];
-        for (int64_t p = x.begin + lane; p < x.end; p += 128) {
-            const int32_t j0 = __ldg(vadj + p * S);
-            const int32_t j1 = p + 32 < x.end ? __ldg(vadj + (p + 32) * S) : -1;
-            const int32_t j2 = p + 64 < x.end ? __ldg(vadj + (p + 64) * S) : -1;
-            const int32_t j3 = p + 96 < x.end ? __ldg(vadj + (p + 96) * S) : -1;
-            // a stale read can only show 1 for a flag another thread just
-            // cleared (flags only go 1 -> 0 here): then it is written twice
-            const bool w0 = !check || __ldcg(alive + j0) != 0;
-            const bool w1 = j1 >= 0 && (!check || __ldcg(alive + j1) != 0);
-            const bool w2 = j2 >= 0 && (!check || __ldcg(alive + j2) != 0);
-            const bool w3 = j3 >= 0 && (!check || __ldcg(alive + j3) != 0);
-            if (w0) alive[j0] = 0;
-            if (w1) alive[j1] = 0;
-            if (w2) alive[j2] = 0;
-            if (w3) alive[j3] = 0;
-        }
+    unsigned long long winpins = 0;
+    for (uint64_t w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
+        const int32_t j = w0 + lane < nw ? a.win[w0 + lane] : -1;
+        warp_win(a, r, j, winpins);
     }
+    block_add_u64(winpins, s_red, &st->winpins);
 }
 
 // Stats row of round r, termination test and next-round decision.
@@ -466,20 +397,22 @@ __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t act
     return cont;
 }
 
-// a4: one thread. Records the round, decides whether another round runs.
-__global__ void k_round_end(RoundArgs a) {
-    if (threadIdx.x != 0) return;
+// a4 (one thread, after every other block of the kill step has finished):
+// records the round, decides whether another round runs, resets the
+// per-round counters.
+__device__ void round_end(const RoundArgs &a) {
     DevState *st = a.st;
     const int r = st->round, par = st->parity;
     const uint32_t nw = st->nwin, next = st->cnt[par ^ 1];
     const int64_t active = r == 1 ? a.n : (int64_t)st->cnt[par];
-    const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, st->kills,
-                                  st->nitems, st->live);
+    const unsigned long long kp = st->kpack;
+    const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, kp >> 32,
+                                  (uint32_t)kp, st->live);
     st->nwin = 0;
-    st->nitems = 0;
+    st->kdone = 0;
     st->rgrab = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
-    st->lpack = st->live = 0;
+    st->lpack = st->live = st->kpack = 0;
     if (cont) {
         st->round = r + 1;
         st->parity = par ^ 1;
@@ -488,6 +421,104 @@ __global__ void k_round_end(RoundArgs a) {
         st->finished = 1;
     }
     if (a.use_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
+}
+
+// a3 + a4: deactivate every entry of every kill range, then end the round.
+// The round's ranges are one concatenated sequence of E entries (item i
+// starts at offset items[i].ebase); each warp takes an equal slice of it
+// (at least kill_chunk entries), finds the item holding its first entry by
+// a 32-way search, and walks its slice 128 entries at a time: a window of
+// 32 consecutive items sits in the lanes, each entry finds its item in the
+// window with five shuffles, and each lane has four entries in flight.
+// From round 2 on most targets are already dead (they sit behind the
+// cursors of other vertices), and on this GPU a random 1-byte load costs
+// less than half of a random 1-byte store, so the flag is read first and
+// only live targets are written. In round 1 every target is live: plain
+// stores. The block that finishes last (a ticket counter; every other
+// block has read the round's state by then) runs round_end.
+template <int S>  // the edge id of list entry p is vadj[p * S]
+__global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
+    __shared__ int s_last;
+    DevState *st = a.st;
+    const unsigned long long kp = st->kpack;
+    const uint32_t ni = (uint32_t)kp;
+    const uint64_t ne = kp >> 32;
+    const bool check = st->round > 1;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    const int32_t *__restrict__ vadj = a.vadj;
+    uint8_t *__restrict__ alive = a.alive;
+    const KillItem *__restrict__ items = a.items;
+    if (ni > 0 && ni <= a.item_cap) {
+        const uint64_t steps = (ne + 31) / 32;
+        uint64_t per = (steps + nwarps - 1) / nwarps;
+        const uint64_t least = (uint64_t)(a.kill_chunk + 31) / 32;
+        if (per < least) per = least;
+        uint64_t q = warp * per * 32;
+        const uint64_t q1 = min(ne, q + per * 32);
+        if (q < q1) {
+            // the item holding entry q: the largest i with items[i].ebase <= q
+            uint32_t lo = 0, hi = ni - 1;
+            while (lo < hi) {
+                const uint32_t stride = (hi - lo) / 32 + 1;
+                const uint64_t p = (uint64_t)lo + (uint64_t)lane * stride;
+                const bool le = p <= hi && __ldg(&items[p].ebase) <= q;
+                const unsigned bm = __ballot_sync(kFull, le);  // lane 0 always set
+                lo += (uint32_t)(31 - __clz(bm)) * stride;
+                hi = min(hi, lo + stride - 1);
+            }
+            uint32_t i = lo;
+            while (q < q1) {
+                const KillItem it = i + lane < ni ? items[i + lane] : KillItem{0u, 0xFFFFFFFFu};
+                const uint64_t wend = (uint64_t)i + 32 < ni ? (uint64_t)__ldg(&items[i + 32].ebase) : ne;
+                const uint64_t stop = min(wend, q1);
+                const uint32_t e1 = __shfl_sync(kFull, it.ebase, 1);
+                for (; q < stop; q += 128) {
+                    // one item covers all 128 entries: no search
+                    const bool one = (uint64_t)e1 >= q + 128;
+                    int32_t jj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint64_t qq = q + 32 * u + lane;
+                        int k = 0;
+                        if (!one) {
+#pragma unroll
+                            for (int d = 16; d > 0; d >>= 1) {
+                                const uint32_t e = __shfl_sync(kFull, it.ebase, k + d);
+                                if ((uint64_t)e <= qq) k += d;
+                            }
+                        }
+                        const uint32_t bg = __shfl_sync(kFull, it.begin, k);
+                        const uint32_t eb = __shfl_sync(kFull, it.ebase, k);
+                        jj[u] = qq < stop ? __ldg(vadj + (uint64_t)(bg + (uint32_t)(qq - eb)) * S) : -1;
+                    }
+                    // a stale read can only show 1 for a flag another thread just
+                    // cleared (flags only go 1 -> 0 here): then it is written twice
+                    bool wr[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) wr[u] = jj[u] >= 0 && (!check || __ldcg(alive + jj[u]) != 0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (wr[u]) alive[jj[u]] = 0;
+                }
+                q = stop;
+                i += 32;
+            }
+        }
+    } else if (ni > a.item_cap && blockIdx.x == 0 && threadIdx.x == 0) {
+        st->fault = 2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->kdone, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        round_end(a);
+    }
 }
 
 __global__ void k_vertex_state(const int4 *vrec, const int32_t *order, int64_t n, int32_t *out) {
@@ -517,10 +548,27 @@ unsigned grid_of(const Handle *h, K kernel, int want) {
     return (unsigned)std::max(1, h->sm_count * b);
 }
 
+void launch_kill(const Handle *h, const RoundArgs &a, cudaStream_t s, int kill_stride) {
+    if (kill_stride == 2) k_kill<2><<<h->kill_grid, kT, 0, s>>>(a);
+    else k_kill<1><<<h->kill_grid, kT, 0, s>>>(a);
+}
+
+void launch_win_kill(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int kill_stride) {
+    if (ev) cudaEventRecord(ev[1], s);
+    k_win<<<h->win_grid, kT, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[2], s);
+    launch_kill(h, a, s, kill_stride);
+    if (ev) {  // the round end is part of the kill kernel: its span is empty
+        cudaEventRecord(ev[3], s);
+        cudaEventRecord(ev[4], s);
+    }
+}
+
+// One round of the fixed order. ev (or null): events 0-4 of a profiled round.
 void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
     k_argmax<<<h->argmax_grid, kT, 0, s>>>(a);
-    launch_win_kill_end(h, a, s, ev);
+    launch_win_kill(h, a, s, ev, 1);
 }
 
 unsigned init_grid(const Handle *h) {
@@ -572,16 +620,8 @@ hm_status build_graph(Handle *h) {
 
 }  // namespace
 
-// a2 - a4 of one round (the part both round loops share).
 void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int kill_stride) {
-    if (ev) cudaEventRecord(ev[1], s);
-    k_win<<<h->win_grid, kT, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[2], s);
-    if (kill_stride == 2) k_kill<2><<<h->kill_grid, kT, 0, s>>>(a);
-    else k_kill<1><<<h->kill_grid, kT, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[3], s);
-    k_round_end<<<1, 32, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[4], s);
+    launch_win_kill(h, a, s, ev, kill_stride);
 }
 
 hm_status capture_chain(Handle *h, cudaGraph_t g, void (*capture)(Handle *, cudaStream_t, void *), void *ctx,
@@ -681,7 +721,7 @@ RoundArgs round_args(const Handle *h) {
 hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
     h->win_cap = std::min(n, m) + 1;
-    h->item_cap = n + h->kappa / kMinKillChunk + 1;
+    h->item_cap = n + 1;  // one kill range per newly matched vertex
     hm_status st;
     if ((st = dalloc(&h->alive, m, s, "alive")) != HM_OK) return st;
     if ((st = dalloc(&h->P, m, s, "P")) != HM_OK) return st;
@@ -779,7 +819,7 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
         for (int k = 0; k < 4; ++k) {
             cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
             ms[HM_K_ARGMAX + k] += t;
-            launches[HM_K_ARGMAX + k] += 1;
+            launches[HM_K_ARGMAX + k] += k == 3 ? 0 : 1;  // the round end is part of the kill kernel
             if (r < max_rounds) round_ms[(int64_t)r * 4 + k] = t;
         }
         if (h->h_st->finished) break;

@@ -34,7 +34,7 @@
 // round in the other buffer, which the next round reuses. Every vertex that
 // proposed a still-live edge is active in the next round and clears it;
 // stale counts are left only on dead edges, which nobody proposes again.
-// The win, kill and round-end kernels of the fixed-order loop (rounds.cu)
+// The win kernel and the kill kernel (which ends the round) of rounds.cu
 // run unchanged on this handle's re-randomised copies of the vertex records
 // and lists: the cursor field stays 0, so the kill range of a matched vertex
 // is its whole (compacted) list, and the kill step (reading every second
@@ -140,14 +140,14 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         st->parity = 0;
         st->cnt[0] = st->cnt[1] = 0;
         st->nwin = 0;
-        st->nitems = 0;
+        st->kdone = 0;
         st->rgrab = 0;
         st->status = HM_OK;
         st->rounds_done = 0;
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = st->live = 0;
+        st->lpack = st->live = st->kpack = 0;
     }
 }
 
@@ -575,7 +575,8 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
         for (int k = 0; k < 4; ++k) {
             cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
             ms[HM_K_ARGMAX + k] += t;
-            launches[HM_K_ARGMAX + k] += k == 0 ? 3 : 1;  // the argmax step is three kernels here
+            // the argmax step is three kernels here; the round end is part of the kill kernel
+            launches[HM_K_ARGMAX + k] += k == 0 ? 3 : (k == 3 ? 0 : 1);
             if (r < max_rounds) round_ms[(int64_t)r * 4 + k] = t;
         }
         if (h->h_st->finished) break;

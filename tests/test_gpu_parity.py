@@ -160,7 +160,8 @@ def test_repeat_profile_and_device_result():
         prof = mt.profile()
         res = mt.result()
         assert np.array_equal(res.edges, o.edges) and res.rounds == o.rounds
-        assert prof["argmax"][1] == prof["kill"][1] == prof["win"][1] >= o.rounds
+        assert prof["argmax"][1] == prof["win"][1] == prof["kill"][1] >= o.rounds
+        assert prof["round_end"][1] == 0  # part of the kill kernel
         mask = torch.zeros(h.m, dtype=torch.uint8, device="cuda")
         mt.result_device(mask)
         torch.cuda.synchronize()

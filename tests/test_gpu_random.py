@@ -139,6 +139,7 @@ def test_switch_modes_and_repeat():
         r = mt.result()
         assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
         assert prof["win"][1] == prof["kill"][1] >= rand.rounds
+        assert prof["round_end"][1] == 0  # part of the kill kernel
         stats = mt.round_stats()
         assert stats[:rand.rounds, WIN].tolist() == rand.round_stats[:, 2].tolist()
         assert np.all(stats[:rand.rounds, PROPOSALS] > 0)
