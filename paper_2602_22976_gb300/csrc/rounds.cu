@@ -447,7 +447,11 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
-    const int32_t *__restrict__ vadj = a.vadj;
+    // re-randomised rounds: round 1 leaves its working copy of the lists
+    // unwritten (every entry is live), so its kill ranges are read from the
+    // immutable lists, at the same positions
+    const int32_t *__restrict__ vadj =
+        (S == 2 && !check) ? reinterpret_cast<const int32_t *>(a.vadjE) : a.vadj;
     uint8_t *__restrict__ alive = a.alive;
     const KillItem *__restrict__ items = a.items;
     if (ni > 0 && ni <= a.item_cap) {

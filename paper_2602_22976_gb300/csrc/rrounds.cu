@@ -16,8 +16,9 @@
 // round 1 streams the lists with no random read at all (every edge is live
 // then); later rounds add one 1-byte live-flag read per entry, from an
 // array indexed by input id (m bytes, L2-resident). Round 1 reads the
-// immutable lists (vadjE) and writes the working copy (vadjR); later rounds
-// compact vadjR in place. Lists are scheduled by length:
+// immutable lists (vadjE) and writes nothing (it keeps every entry); round 2
+// reads vadjE and writes the compacted lists to the working copy (vadjR);
+// later rounds compact vadjR in place. Lists are scheduled by length:
 //   - at most kLong entries: the 32 vertices of a warp tile are scanned as
 //     one concatenated sequence, kU steps of 32 entries at a time (all their
 //     loads in flight together; segmented maximum and ballot compaction),
@@ -26,19 +27,25 @@
 //     out the queue slot and the first chunk); k_rlong scans the chunks of
 //     kChunk entries with one warp each and combines them per list with a
 //     64-bit atomicMax; k_rfin turns each list's maximum into the vertex's
-//     proposal. Long lists are not compacted: their part of vadjR is
-//     copied once when the handle first runs this mode and never written.
+//     proposal. Long lists are not compacted: they are scanned from vadjE,
+//     and their part of vadjR (read by the kill step) is copied once when
+//     the handle first runs this mode and never written.
 // Proposals use the P counter of Alg. 1 counted up and double-buffered by
 // round parity: a vertex adds 1 to P_r[T[v]], the edge wins when the count
 // reaches |e|, and the vertex clears the entry it counted in the previous
 // round in the other buffer, which the next round reuses. Every vertex that
 // proposed a still-live edge is active in the next round and clears it;
 // stale counts are left only on dead edges, which nobody proposes again.
+// The clear is a plain store: all vertices of a large edge clear the same
+// word, and same-address stores cost far less than same-address atomics
+// (an undo by atomic add measured 5-30 % slower per round). T[v] and the
+// winner list hold relabelled ids j.
 // The win kernel and the kill kernel (which ends the round) of rounds.cu
-// run unchanged on this handle's re-randomised copies of the vertex records
-// and lists: the cursor field stays 0, so the kill range of a matched vertex
-// is its whole (compacted) list, and the kill step (reading every second
-// word: the edge ids of the pairs) clears the flags of the input ids there.
+// run on this handle's re-randomised vertex records and lists: the cursor
+// field stays 0, so the kill range of a matched vertex is its whole
+// (compacted) list, and the kill step (reading every second word: the edge
+// ids of the pairs; from vadjE in round 1) clears the flags of the input ids
+// there.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -98,8 +105,8 @@ __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
     return (int32_t)(0xFFFFFFFFu - (uint32_t)k);
 }
 
-// Proposal of vertex v for edge j (relabelled id) in round r: counts in the
-// round's buffer; returns whether v completed the count (j wins).
+// Proposal of a vertex for edge j (relabelled id) in round r: counts in the
+// round's buffer; returns whether it completed the count (j wins).
 __device__ __forceinline__ bool propose(const RoundArgs &a, uint32_t *Pc, int32_t j) {
     const uint32_t size = (uint32_t)(a.eoffj[j + 1] - a.eoffj[j]);
     return atomicAdd(Pc + j, 1u) + 1u == size;
@@ -172,7 +179,10 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
     uint32_t *Pc = (r & 1) ? a.P2 : a.P;  // counts of this round
     uint32_t *Po = (r & 1) ? a.P : a.P2;  // counts of the previous round
-    const int2 *src = r == 1 ? a.vadjE : a.vadjR;
+    // round 1 keeps every entry: it reads the immutable lists and writes
+    // nothing; round 2 compacts them into the working copy; later rounds
+    // compact the working copy in place
+    const int2 *src = r <= 2 ? a.vadjE : a.vadjR;
     int2 *dst = a.vadjR;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                     opre[u] = __shfl_sync(kFull, pre, x);
                     ob[u] = (int64_t)(uint32_t)__shfl_sync(kFull, rec.z, x);
                 }
-                // plain loads: from round 2 on this kernel rewrites the lists behind the reads
+                // plain loads: from round 3 on this kernel rewrites the lists behind the reads
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const uint32_t p = s0 + 32 * u + lane;
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                         const unsigned seg_lt = lt & ~((1u << sst) - 1u);
                         const unsigned lm = __ballot_sync(kFull, lv);
                         const uint32_t carried = __shfl_sync(kFull, live, o[u]);
-                        if (lv) dst[ob[u] + carried + __popc(lm & seg_lt)] = ev[u];  // compaction
+                        if (lv && r > 1) dst[ob[u] + carried + __popc(lm & seg_lt)] = ev[u];  // compaction
                         // segmented running maximum over the step
                         unsigned long long mx = key;
 #pragma unroll
@@ -342,7 +352,7 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
             const int64_t e = min(lb + (int64_t)(uint32_t)rec.w, b + (int64_t)kChunk);
             unsigned long long mx = 0;
             for (int64_t p = b + lane; p < e; p += 32) {
-                const int2 x = __ldg(a.vadjR + p);  // long lists are only read here
+                const int2 x = __ldg(a.vadjE + p);  // long lists are never compacted
                 if (r == 1 || __ldg(a.alive + x.x)) {
                     const unsigned long long k = round_key(a, r, (uint32_t)x.x, __int_as_float(x.y));
                     if (k > mx) mx = k;

@@ -263,3 +263,21 @@ def test_full_size_powerlaw():
 def test_full_size_unweighted():
     """n=4M, m=8M, |e| ~ U{2..8}, seeded hash priority."""
     assert_parity(synth.unweighted())
+
+
+def test_each_list_entry_touched_once():
+    """The paper compacts the hypergraph after every round (Sec. 4.3) so that
+    the whole run costs O(kappa) work. The cursor design reaches that bound
+    without moving data: every entry of every vertex list is either skipped
+    once by its vertex's cursor (the argmax step) or deactivated once by the
+    kill step, so over the whole run the two counters add up to kappa
+    exactly."""
+    adv = hmlib.STAT_COLUMNS.index("advance")
+    kills = hmlib.STAT_COLUMNS.index("kills")
+    cases = [synth.large(seed=5, n=300_000, m=600_000), synth.small(seed=3),
+             synth.unweighted(seed=2, n=100_000, m=200_000),
+             synth.from_edges(5, [[0, 1], [1, 2], [2, 3], [3, 4]], None, seed=1)]
+    for h in cases:
+        res, stats, _ = run_gpu(h)
+        assert res.status == OK
+        assert int(stats[:, adv].sum() + stats[:, kills].sum()) == h.kappa
