@@ -199,10 +199,14 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
 // the edge joins M (input numbering, with its round), every vertex of it is
 // marked matched, and each vertex emits one kill range: its list from the
 // cursor on (the winner's own entry included, which kills the winner). The
-// pins of the warp's winners are spread over the lanes 32 at a time; items
-// and their entries are reserved with one 64-bit atomic per 32 pins, so the
-// item order and the entry offsets ascend together. All 32 lanes must call.
+// pins of the warp's winners are spread over the lanes, 128 at a time (four
+// per lane, their loads in flight together); the items of those pins and
+// their entries are reserved with one 64-bit atomic, so the item order and
+// the entry offsets ascend together. The reservation counter is one word
+// for the whole GPU: one atomic per 128 pins keeps it from serialising the
+// step. All 32 lanes must call.
 __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, unsigned long long &winpins) {
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     uint32_t len = 0;
     int64_t b = 0;
@@ -218,44 +222,66 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
     const uint32_t exc = inc - len;
     const uint32_t total = __shfl_sync(kFull, inc, 31);
     const unsigned lt = lanemask_lt();
-    for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-        const uint32_t q = p0 + lane;
-        // owner of pin q: the largest lane k with exc_k <= q (exc ascends)
-        int k = 0;
+    for (uint32_t p0 = 0; p0 < total; p0 += 32 * U) {
+        int32_t v[U], jk[U];
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const uint32_t e = __shfl_sync(kFull, exc, k + d);
-            if (e <= q) k += d;
+        for (int u = 0; u < U; ++u) {
+            const uint32_t q = p0 + 32 * u + lane;
+            // owner of pin q: the largest lane k with exc_k <= q (exc ascends)
+            int k = 0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const uint32_t e = __shfl_sync(kFull, exc, k + d);
+                if (e <= q) k += d;
+            }
+            jk[u] = __shfl_sync(kFull, j, k);
+            const int64_t bk = __shfl_sync(kFull, b, k);
+            const uint32_t ek = __shfl_sync(kFull, exc, k);
+            v[u] = q < total ? __ldg(a.pinsj + bk + (q - ek)) : -1;
         }
-        const int32_t jk = __shfl_sync(kFull, j, k);
-        const int64_t bk = __shfl_sync(kFull, b, k);
-        const uint32_t ek = __shfl_sync(kFull, exc, k);
-        uint32_t ibeg = 0, ilen = 0;
-        if (q < total) {
-            const int32_t v = __ldg(a.pinsj + bk + (q - ek));
-            const int4 rec = a.vrec[v];
-            const uint32_t c = (uint32_t)rec.z + (uint32_t)rec.y;
-            const uint32_t end = (uint32_t)rec.z + (uint32_t)rec.w;
-            // T[v] must be the winner: v chose it, and nothing moves it
-            if (rec.x == jk && c < end) {
-                reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurMatched, 0);
-                ibeg = c;
-                ilen = end - c;
-            } else {
-                a.st->fault = 1;
+        uint32_t ibeg[U], ilen[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ibeg[u] = 0;
+            ilen[u] = 0;
+            if (v[u] >= 0) {
+                const int4 rec = a.vrec[v[u]];
+                const uint32_t c = (uint32_t)rec.z + (uint32_t)rec.y;
+                const uint32_t end = (uint32_t)rec.z + (uint32_t)rec.w;
+                // T[v] must be the winner: v chose it, and nothing moves it
+                if (rec.x == jk[u] && c < end) {
+                    reinterpret_cast<int2 *>(a.vrec + v[u])[0] = make_int2(kCurMatched, 0);
+                    ibeg[u] = c;
+                    ilen[u] = end - c;
+                } else {
+                    a.st->fault = 1;
+                }
             }
         }
-        const unsigned has = __ballot_sync(kFull, ilen > 0);
-        const uint32_t iinc = warp_inclusive_scan(ilen);
-        const uint32_t itot = __shfl_sync(kFull, iinc, 31);
+        unsigned has[U];
+        uint32_t iinc[U], ibase[U], ebase[U];
+        uint32_t nitems = 0, nent = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            has[u] = __ballot_sync(kFull, ilen[u] > 0);
+            iinc[u] = warp_inclusive_scan(ilen[u]);
+            ibase[u] = nitems;
+            ebase[u] = nent;
+            nitems += (uint32_t)__popc(has[u]);
+            nent += __shfl_sync(kFull, iinc[u], 31);
+        }
         unsigned long long old = 0;
-        if (lane == 0 && has)
-            old = atomicAdd(&a.st->kpack, ((unsigned long long)itot << 32) | (unsigned long long)__popc(has));
+        if (lane == 0 && nitems)
+            old = atomicAdd(&a.st->kpack, ((unsigned long long)nent << 32) | (unsigned long long)nitems);
         old = __shfl_sync(kFull, old, 0);
-        if (ilen) {
-            const uint64_t idx = (uint64_t)(uint32_t)old + (uint32_t)__popc(has & lt);
-            if (idx < a.item_cap) a.items[idx] = KillItem{ibeg, (uint32_t)(old >> 32) + iinc - ilen};
-            else a.st->fault = 2;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (ilen[u]) {
+                const uint64_t idx = (uint64_t)(uint32_t)old + ibase[u] + (uint32_t)__popc(has[u] & lt);
+                const uint32_t eb = (uint32_t)(old >> 32) + ebase[u] + iinc[u] - ilen[u];
+                if (idx < a.item_cap) a.items[idx] = KillItem{ibeg[u], eb};
+                else a.st->fault = 2;
+            }
         }
     }
 }
