@@ -28,6 +28,7 @@ struct CreateErr {
     uint32_t flags;
     uint32_t pad;
     unsigned long long first[4];  // first offending index per error kind
+    unsigned long long max_size;  // largest edge size
 };
 
 __device__ __forceinline__ void report(CreateErr *err, uint32_t kind, int bit, unsigned long long idx) {
@@ -35,15 +36,19 @@ __device__ __forceinline__ void report(CreateErr *err, uint32_t kind, int bit, u
     atomicMin(&err->first[bit], idx);
 }
 
-// Sec. 2.1: every edge is a non-empty set, weights are positive.
+// Sec. 2.1: every edge is a non-empty set, weights are positive. Also
+// finds the largest edge size (it decides the width of the P counters).
 __global__ void k_validate(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
                            const float *__restrict__ w, int64_t n, int64_t m, uint64_t kappa,
                            CreateErr *err) {
     const uint64_t total = (uint64_t)(m > (int64_t)kappa ? m : (int64_t)kappa);
+    unsigned long long mx = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         if (i < (uint64_t)m) {
-            if (eoff[i + 1] <= eoff[i]) report(err, kErrEdgeRange, 0, i);
+            const int64_t sz = eoff[i + 1] - eoff[i];
+            if (sz <= 0) report(err, kErrEdgeRange, 0, i);
+            else if ((unsigned long long)sz > mx) mx = (unsigned long long)sz;
             if (w) {
                 const uint32_t b = __float_as_uint(w[i]);
                 // finite and > 0: sign clear, not zero, exponent below all-ones
@@ -55,6 +60,12 @@ __global__ void k_validate(const int64_t *__restrict__ eoff, const int32_t *__re
             if (p < 0 || (int64_t)p >= n) report(err, kErrPin, 1, i);
         }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, d);
+        if (y > mx) mx = y;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&err->max_size, mx);
 }
 
 // MurmurHash3 32-bit finaliser (Appleby): a bijection on 32-bit words.
@@ -274,6 +285,7 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
         set_error(buf);
         return HM_EINVAL;
     }
+    h->p16 = herr.max_size <= 0xFFFFull;
     cudaEventRecord(ev.e[1], s);
 
     // 2. order on edges: stable sort of ~priority over edges in id order

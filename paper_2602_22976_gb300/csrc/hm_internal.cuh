@@ -10,7 +10,11 @@
 //                       decreasing priority (V_p)
 //   alive  uint8[m]     1 = live edge (soft delete, Sec. 3.1)
 //   P      uint32[m]    pins of e that have not chosen e yet; e wins when it
-//                       reaches 0 (the P counter of Alg. 1 / Sec. 4.1, counted down)
+//                       reaches 0 (the P counter of Alg. 1 / Sec. 4.1, counted
+//                       down). When no edge has more than 65535 pins the
+//                       counters are 16 bits wide, two to a word (edge e in
+//                       half e & 1 of word e >> 1): half the footprint, so
+//                       more of them stay in L2
 //   vrec   int4[n]      per-vertex record {T[v] as an edge j, cursor of T[v]
 //                       relative to the list start, list start, degree}
 //                       (Alg. 3's T plus V_id); T[v] = kCurMatched once v is
@@ -118,6 +122,7 @@ struct RoundArgs {
     int64_t n;
     int64_t m;
     int64_t cap;           // round cap
+    int p16;               // P holds 16-bit counters, two per word
     uint64_t item_cap;     // capacity of items
     uint64_t win_cap;      // capacity of win
     cudaGraphConditionalHandle cond;
@@ -139,6 +144,7 @@ struct Handle {
     int64_t n = 0, m = 0;
     uint64_t kappa = 0;
     bool weighted = true;
+    bool p16 = false;           // every edge has at most 65535 pins: 16-bit P counters
     uint64_t seed = 0;
     int sm_count = 0;
     // device buffers (owned)

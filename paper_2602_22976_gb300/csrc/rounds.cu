@@ -73,8 +73,14 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
     for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < total; i += (int64_t)gridDim.x * kT) {
         if (i < a.m) {
             a.alive[i] = 1;
-            a.P[i] = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
             a.inM[i] = 0;
+            if (!a.p16) {
+                a.P[i] = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
+            } else if ((i & 1) == 0) {  // the word of edges i and i + 1
+                const uint32_t lo = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
+                const uint32_t hi = i + 1 < a.m ? (uint32_t)(a.eoffj[i + 2] - a.eoffj[i + 1]) : 0u;
+                a.P[i >> 1] = lo | (hi << 16);
+            }
         }
         if (i < a.n) reinterpret_cast<int2 *>(a.vrec + i)[0] = make_int2(a.firstj[i], 0);
     }
@@ -330,7 +336,12 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
             bool w = false;
             if (nb >= 0) {
                 ++props;
-                w = atomicSub(&a.P[nb], 1u) == 1u;
+                if (a.p16) {  // a count never goes below 0, so no borrow crosses halves
+                    const int sh = (nb & 1) * 16;
+                    w = ((atomicSub(&a.P[nb >> 1], 1u << sh) >> sh) & 0xFFFFu) == 1u;
+                } else {
+                    w = atomicSub(&a.P[nb], 1u) == 1u;
+                }
             }
             const unsigned km = __ballot_sync(kFull, keep);
             if (keep) out[base + kept + __popc(km & lt)] = v;
@@ -740,6 +751,7 @@ RoundArgs round_args(const Handle *h) {
     a.n = h->n;
     a.m = h->m;
     a.cap = h->cap;
+    a.p16 = h->p16 ? 1 : 0;
     a.item_cap = h->item_cap;
     a.wround = h->wround;
     a.kill_chunk = h->cfg.kill_chunk;

@@ -281,3 +281,18 @@ def test_each_list_entry_touched_once():
         res, stats, _ = run_gpu(h)
         assert res.status == OK
         assert int(stats[:, adv].sum() + stats[:, kills].sum()) == h.kappa
+
+
+@pytest.mark.parametrize("big_weight", [1.0, 1e-3])
+def test_edge_wider_than_16_bit_counters(big_weight):
+    """One edge of 70,000 pins: the P counters cannot be 16 bits wide, so the
+    32-bit counters run. Heavy, the big edge wins in round 1; light, it dies
+    to a small neighbour."""
+    rng = np.random.default_rng(7)
+    n = 100_000
+    edges = [np.sort(rng.choice(n, 70_000, replace=False)).tolist()]
+    edges += [rng.choice(n, int(rng.integers(2, 6)), replace=False).tolist() for _ in range(30_000)]
+    w = rng.uniform(0.01, 0.99, size=len(edges)).astype(np.float32)
+    w[0] = big_weight
+    h = synth.from_edges(n, edges, w.tolist(), seed=1)
+    assert_parity(h)
