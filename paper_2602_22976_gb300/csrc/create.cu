@@ -36,30 +36,43 @@ __device__ __forceinline__ void report(CreateErr *err, uint32_t kind, int bit, u
     atomicMin(&err->first[bit], idx);
 }
 
+__device__ __forceinline__ void check_pin(int32_t p, int64_t n, uint64_t i, CreateErr *err) {
+    if (p < 0 || (int64_t)p >= n) report(err, kErrPin, 1, i);
+}
+
 // Sec. 2.1: every edge is a non-empty set, weights are positive. Also
 // finds the largest edge size (it decides the width of the P counters).
+// Pins are read 16 bytes at a time when the array is 16-byte aligned.
 __global__ void k_validate(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
                            const float *__restrict__ w, int64_t n, int64_t m, uint64_t kappa,
                            CreateErr *err) {
-    const uint64_t total = (uint64_t)(m > (int64_t)kappa ? m : (int64_t)kappa);
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long mx = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        if (i < (uint64_t)m) {
-            const int64_t sz = eoff[i + 1] - eoff[i];
-            if (sz <= 0) report(err, kErrEdgeRange, 0, i);
-            else if ((unsigned long long)sz > mx) mx = (unsigned long long)sz;
-            if (w) {
-                const uint32_t b = __float_as_uint(w[i]);
-                // finite and > 0: sign clear, not zero, exponent below all-ones
-                if (b == 0u || b >= 0x7F800000u) report(err, kErrWeight, 2, i);
-            }
-        }
-        if (i < kappa) {
-            const int32_t p = pins[i];
-            if (p < 0 || (int64_t)p >= n) report(err, kErrPin, 1, i);
+    for (uint64_t i = tid; i < (uint64_t)m; i += nth) {
+        const int64_t sz = eoff[i + 1] - eoff[i];
+        if (sz <= 0) report(err, kErrEdgeRange, 0, i);
+        else if ((unsigned long long)sz > mx) mx = (unsigned long long)sz;
+        if (w) {
+            const uint32_t b = __float_as_uint(w[i]);
+            // finite and > 0: sign clear, not zero, exponent below all-ones
+            if (b == 0u || b >= 0x7F800000u) report(err, kErrWeight, 2, i);
         }
     }
+    uint64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(pins) & 15u) == 0) {
+        const uint64_t n4 = kappa / 4;
+        const int4 *p4 = reinterpret_cast<const int4 *>(pins);
+        for (uint64_t q = tid; q < n4; q += nth) {
+            const int4 x = __ldg(p4 + q);
+            check_pin(x.x, n, 4 * q, err);
+            check_pin(x.y, n, 4 * q + 1, err);
+            check_pin(x.z, n, 4 * q + 2, err);
+            check_pin(x.w, n, 4 * q + 3, err);
+        }
+        done = 4 * n4;
+    }
+    for (uint64_t i = done + tid; i < kappa; i += nth) check_pin(__ldg(pins + i), n, i, err);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, d);
@@ -103,21 +116,25 @@ __global__ void k_priority(const float *__restrict__ w, uint32_t salt, int64_t m
     }
 }
 
+// Size and first input pin of every edge, in j order.
 __global__ void k_sizes_j(const int64_t *__restrict__ eoff, const uint32_t *__restrict__ order,
-                          int64_t m, int64_t *__restrict__ szj) {
+                          int64_t m, int64_t *__restrict__ szj, int64_t *__restrict__ srcj) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
          j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[j];
-        szj[j] = eoff[e + 1] - eoff[e];
+        const int64_t b = eoff[e];
+        szj[j] = eoff[e + 1] - b;
+        srcj[j] = b;
     }
 }
 
 // Pins of input edge order[j] -> pinsj[eoffj[j] ..]; the same slots of
 // jval receive j. Output-driven: a block fills kRelTile consecutive output
 // slots, loads the offsets of exactly the edges covering them (first[t] is
-// the edge containing the tile's first slot), locates each slot's edge by
-// binary search in shared memory, and writes both outputs coalesced
-// whatever the edge sizes.
+// the edge containing the tile's first slot) and where their pins start in
+// the input (srcj), locates each slot's edge by binary search in shared
+// memory, and writes both outputs coalesced whatever the edge sizes. One
+// tile per block: the GPU keeps many tiles' dependent loads in flight.
 constexpr int kRelTile = 2048;
 
 // first[t] = the edge that contains output slot t*kRelTile.
@@ -131,55 +148,73 @@ __global__ void k_tile_first(const int64_t *__restrict__ eoffj, int64_t m, uint6
     }
 }
 
-__global__ void __launch_bounds__(kT) k_relabel(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pins,
-                                               const uint32_t *__restrict__ order,
+__global__ void __launch_bounds__(kT) k_relabel(const int32_t *__restrict__ pins, const int64_t *__restrict__ srcj,
                                                const int64_t *__restrict__ eoffj, const int32_t *__restrict__ first,
                                                int64_t m, uint64_t kappa, uint64_t ntiles,
                                                int32_t *__restrict__ pinsj, uint32_t *__restrict__ jval) {
     __shared__ int64_t s_off[kRelTile + 1];  // eoffj of the tile's edges
-    __shared__ int64_t s_src[kRelTile];      // eoff of their input edges
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t p0 = t * kRelTile;
-        const uint64_t p1 = p0 + kRelTile < kappa ? p0 + kRelTile : kappa;
-        const int64_t j0 = first[t];
-        const int64_t j1 = t + 1 < ntiles ? first[t + 1] : m - 1;  // last edge touching the tile
-        const int ne = (int)(j1 - j0 + 1);                          // <= kRelTile + 1
-        for (int k = threadIdx.x; k <= ne && k <= kRelTile; k += kT) {
-            s_off[k] = eoffj[j0 + k];
-            if (k < ne && k < kRelTile) s_src[k] = eoff[order[j0 + k]];
+    __shared__ int64_t s_src[kRelTile];      // their first input pin
+    const uint64_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    const uint64_t p0 = t * kRelTile;
+    const uint64_t p1 = p0 + kRelTile < kappa ? p0 + kRelTile : kappa;
+    const int64_t j0 = first[t];
+    const int64_t j1 = t + 1 < ntiles ? first[t + 1] : m - 1;  // last edge touching the tile
+    const int ne = (int)(j1 - j0 + 1);                          // <= kRelTile + 1
+    for (int k = threadIdx.x; k <= ne && k <= kRelTile; k += kT) {
+        s_off[k] = eoffj[j0 + k];
+        if (k < ne && k < kRelTile) s_src[k] = srcj[j0 + k];
+    }
+    __syncthreads();
+    const int hi0 = (ne < kRelTile ? ne : kRelTile) - 1;
+    for (uint64_t p = p0 + threadIdx.x; p < p1; p += kT) {
+        int lo = 0, hi = hi0;  // last k with s_off[k] <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((uint64_t)s_off[mid] <= p) lo = mid; else hi = mid - 1;
         }
-        __syncthreads();
-        const int hi0 = (ne < kRelTile ? ne : kRelTile) - 1;
-        for (uint64_t p = p0 + threadIdx.x; p < p1; p += kT) {
-            int lo = 0, hi = hi0;  // last k with s_off[k] <= p
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((uint64_t)s_off[mid] <= p) lo = mid; else hi = mid - 1;
-            }
-            pinsj[p] = pins[s_src[lo] + (int64_t)(p - (uint64_t)s_off[lo])];
-            jval[p] = (uint32_t)(j0 + lo);
-        }
-        __syncthreads();
+        pinsj[p] = pins[s_src[lo] + (int64_t)(p - (uint64_t)s_off[lo])];
+        jval[p] = (uint32_t)(j0 + lo);
     }
 }
 
 // voff from the vertex-sorted pin list: position i starts the segments of
 // the vertices (sv[i-1], sv[i]] (degree-0 vertices get empty segments).
 // firstj[v] = the first entry of v's list (or -2 for degree 0). Also flags a
-// vertex repeated inside one edge (equal (v, j) neighbours).
+// vertex repeated inside one edge (equal (v, j) neighbours). Four positions
+// per thread, read 16 bytes at a time.
+__device__ __forceinline__ void voff_at(uint64_t i, uint32_t prev_v, uint32_t v, uint32_t prev_j, uint32_t j,
+                                        uint64_t kappa, int64_t n, int64_t *__restrict__ voff,
+                                        int32_t *__restrict__ firstj, CreateErr *err) {
+    const int64_t lo = i == 0 ? 0 : (int64_t)prev_v + 1;
+    const int64_t hi = i == kappa ? n : (int64_t)v;
+    for (int64_t x = lo; x <= hi; ++x) {
+        voff[x] = (int64_t)i;
+        if (x < n) firstj[x] = (x == hi && i < kappa) ? (int32_t)j : -2;
+    }
+    if (i > 0 && i < kappa && v == prev_v && j == prev_j) report(err, kErrDup, 3, i);
+}
+
 __global__ void k_voff(const uint32_t *__restrict__ sv, const uint32_t *__restrict__ vadj,
                        uint64_t kappa, int64_t n, int64_t *__restrict__ voff,
                        int32_t *__restrict__ firstj, CreateErr *err) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= kappa;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const int64_t lo = i == 0 ? 0 : (int64_t)sv[i - 1] + 1;
-        const int64_t hi = i == kappa ? n : (int64_t)sv[i];
-        for (int64_t v = lo; v <= hi; ++v) {
-            voff[v] = (int64_t)i;
-            if (v < n) firstj[v] = (v == hi && i < kappa) ? (int32_t)vadj[i] : -2;
-        }
-        if (i > 0 && i < kappa && sv[i] == sv[i - 1] && vadj[i] == vadj[i - 1])
-            report(err, kErrDup, 3, i);
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = kappa / 4;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sv);
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(vadj);
+    for (uint64_t q = tid; q < n4; q += nth) {
+        const uint4 v = __ldg(s4 + q), j = __ldg(a4 + q);
+        const uint32_t pv = q ? __ldg(sv + 4 * q - 1) : 0u, pj = q ? __ldg(vadj + 4 * q - 1) : 0u;
+        voff_at(4 * q, pv, v.x, pj, j.x, kappa, n, voff, firstj, err);
+        voff_at(4 * q + 1, v.x, v.y, j.x, j.y, kappa, n, voff, firstj, err);
+        voff_at(4 * q + 2, v.y, v.z, j.y, j.z, kappa, n, voff, firstj, err);
+        voff_at(4 * q + 3, v.z, v.w, j.z, j.w, kappa, n, voff, firstj, err);
+    }
+    for (uint64_t i = 4 * n4 + tid; i <= kappa; i += nth) {
+        const uint32_t pv = i ? sv[i - 1] : 0u, pj = i ? vadj[i - 1] : 0u;
+        const uint32_t v = i < kappa ? sv[i] : 0u, j = i < kappa ? vadj[i] : 0u;
+        voff_at(i, pv, v, pj, j, kappa, n, voff, firstj, err);
     }
 }
 
@@ -308,13 +343,14 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     cudaEventRecord(ev.e[2], s);
 
     // 3. edge CSR in j order
-    int64_t *szj = nullptr, *i64scratch = nullptr;
+    int64_t *szj = nullptr, *srcj = nullptr, *i64scratch = nullptr;
     if ((st = dalloc(&h->eoffj, (uint64_t)m + 1, s, "eoffj")) != HM_OK ||
         (st = dalloc(&h->pinsj, kappa, s, "pinsj")) != HM_OK ||
         (st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
+        (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
         (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
         return st;
-    k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj);
+    k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj, srcj);
     ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
     tmp.drop(szj);
@@ -326,9 +362,10 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
         int32_t *first = nullptr;
         if ((st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK) return st;
         k_tile_first<<<gm, kT, 0, s>>>(h->eoffj, m, ntiles, first);
-        k_relabel<<<grid_for(ntiles * kT, kT, h->sm_count, 8), kT, 0, s>>>(
-            eoff, pins, order_u, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
+        if (ntiles > 0)
+            k_relabel<<<(unsigned)ntiles, kT, 0, s>>>(pins, srcj, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
         tmp.drop(first);
+        tmp.drop(srcj);
     }
     cudaEventRecord(ev.e[3], s);
 

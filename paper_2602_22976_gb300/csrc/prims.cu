@@ -8,7 +8,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 8;
-constexpr int kTile = kThreads * kItems;  // 4096 elements per block
+constexpr int kTile = kThreads * kItems;  // 2048 elements per block (scan, compaction)
 constexpr int kWarps = kThreads / 32;
 static_assert(kThreads == 256, "histogram and scatter kernels use one thread per digit");
 
@@ -117,53 +117,135 @@ cudaError_t exclusive_scan_t(const T *in, T *out, uint64_t n, T *total, T *scrat
 }
 
 // ------------------------------------------------------------------ radix sort
+// LSD radix sort of 32-bit keys with 32-bit values, 8-bit digits. A pass:
+//  1. rs_hist_k: every tile of kRTile keys counts its digits into one
+//     256-entry row of a tile-major histogram (a coalesced 1 KB write);
+//  2. rs_scan_{a,b,c}_k: the histogram becomes the output offset of every
+//     (tile, digit) run - digits in order, and inside a digit the tiles in
+//     order, which is what makes the pass stable - with every access a
+//     coalesced row of 256 words (a: per-digit sums over blocks of
+//     kScanTiles tiles; b: one block scans those sums and the digit totals;
+//     c: running offsets inside each block of tiles);
+//  3. rs_scatter_k: every tile ranks its keys (stable inside the tile),
+//     regroups them by digit in shared memory and writes each digit's run
+//     to its offset with consecutive threads.
+constexpr int kRI = 16;                 // keys per thread
+constexpr int kRTile = kThreads * kRI;  // 4096 keys per tile
+constexpr int kScanTiles = 256;         // tiles per block of the offset scan
 
-__global__ void __launch_bounds__(kThreads) rs_hist_k(const uint32_t *keys, uint64_t n, int shift,
-                                                      uint32_t *hist, uint32_t ntiles) {
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;  // kThreads == 256
+__global__ void __launch_bounds__(kThreads) rs_hist_k(const uint32_t *__restrict__ keys, uint64_t n, int shift,
+                                                      uint32_t *__restrict__ hist) {
+    __shared__ uint32_t cnt[kWarps][256];  // one sub-histogram per warp: fewer same-address atomics
+    for (int d = threadIdx.x; d < kWarps * 256; d += kThreads) (&cnt[0][0])[d] = 0;
     __syncthreads();
-    const uint64_t tbase = (uint64_t)blockIdx.x * kTile;
-#pragma unroll 4
-    for (int k = 0; k < kItems; ++k) {
-        uint64_t i = tbase + (uint64_t)k * kThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+    uint32_t *mine = cnt[threadIdx.x >> 5];
+    const uint64_t tbase = (uint64_t)blockIdx.x * kRTile;
+    if (tbase + kRTile <= n) {  // full tile: 16-byte loads
+        const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + tbase);
+#pragma unroll
+        for (int k = 0; k < kRI / 4; ++k) {
+            const uint4 x = __ldg(k4 + k * kThreads + threadIdx.x);
+            atomicAdd(&mine[(x.x >> shift) & 255u], 1u);
+            atomicAdd(&mine[(x.y >> shift) & 255u], 1u);
+            atomicAdd(&mine[(x.z >> shift) & 255u], 1u);
+            atomicAdd(&mine[(x.w >> shift) & 255u], 1u);
+        }
+    } else {
+        for (int k = 0; k < kRI; ++k) {
+            const uint64_t i = tbase + (uint64_t)k * kThreads + threadIdx.x;
+            if (i < n) atomicAdd(&mine[(__ldg(keys + i) >> shift) & 255u], 1u);
+        }
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sum += cnt[w][threadIdx.x];
+    hist[(uint64_t)blockIdx.x * 256 + threadIdx.x] = sum;
+}
+
+// part[b][d] = sum of hist[t][d] over the tiles t of block b.
+__global__ void __launch_bounds__(kThreads) rs_scan_a_k(const uint32_t *__restrict__ hist, uint64_t ntiles,
+                                                        uint32_t *__restrict__ part) {
+    const uint64_t t0 = (uint64_t)blockIdx.x * kScanTiles;
+    const uint64_t t1 = t0 + kScanTiles < ntiles ? t0 + kScanTiles : ntiles;
+    uint32_t s = 0;
+#pragma unroll 8
+    for (uint64_t t = t0; t < t1; ++t) s += hist[t * 256 + threadIdx.x];
+    part[(uint64_t)blockIdx.x * 256 + threadIdx.x] = s;
+}
+
+// One block: part[b][d] <- (keys of digits < d) + (keys of digit d in blocks < b).
+__global__ void __launch_bounds__(kThreads) rs_scan_b_k(uint32_t *part, uint64_t nb) {
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+    for (uint64_t b0 = 0; b0 < nb; b0 += 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = b0 + k < nb ? part[(b0 + k) * 256 + d] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (b0 + k < nb) part[(b0 + k) * 256 + d] = run;
+            run += x[k];
+        }
+    }
+    __shared__ uint32_t tot;
+    const uint32_t base = block_exclusive_scan<uint32_t>(run, &tot);
+    for (uint64_t b = 0; b < nb; ++b) part[b * 256 + d] += base;
+}
+
+// hist[t][d] <- output offset of the run of digit d from tile t.
+__global__ void __launch_bounds__(kThreads) rs_scan_c_k(uint32_t *hist, uint64_t ntiles, const uint32_t *part) {
+    const uint64_t t0 = (uint64_t)blockIdx.x * kScanTiles;
+    const uint64_t t1 = t0 + kScanTiles < ntiles ? t0 + kScanTiles : ntiles;
+    const int d = threadIdx.x;
+    uint32_t run = part[(uint64_t)blockIdx.x * 256 + d];
+    for (uint64_t t = t0; t < t1; t += 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = t + k < t1 ? hist[(t + k) * 256 + d] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (t + k < t1) hist[(t + k) * 256 + d] = run;
+            run += x[k];
+        }
+    }
 }
 
 // Stable scatter of one tile. Warp w owns the contiguous sub-tile
-// [w*512, (w+1)*512) and walks it 32 elements at a time; lanes with equal
+// [w*512, (w+1)*512) and walks it 32 keys at a time; lanes with equal
 // digits are ranked with __match_any_sync, so equal keys keep input order
 // inside the warp, and warps are ordered by a per-digit prefix over warps.
 // The tile is first rearranged in shared memory into digit order, then
 // written out by consecutive threads, so each run of equal digits becomes
 // one coalesced segment of the output.
-__global__ void __launch_bounds__(kThreads) rs_scatter_k(const uint32_t *kin, const uint32_t *vin,
-                                                         uint32_t *kout, uint32_t *vout, uint64_t n,
-                                                         int shift, const uint32_t *offs,
-                                                         uint32_t ntiles) {
-    constexpr int kSub = 32 * kItems;
+__global__ void __launch_bounds__(kThreads, 3) rs_scatter_k(const uint32_t *__restrict__ kin,
+                                                         const uint32_t *__restrict__ vin,
+                                                         uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                         uint64_t n, int shift, const uint32_t *__restrict__ offs) {
+    constexpr int kSub = 32 * kRI;
     __shared__ uint32_t wcnt[kWarps][256];
     __shared__ uint32_t dstart[256];  // first tile-local slot of each digit
     __shared__ uint32_t goff[256];    // global position of each digit's run from this tile
-    __shared__ uint32_t skey[kTile], sval[kTile];
+    __shared__ uint32_t skey[kRTile], sval[kRTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < kWarps * 256; d += kThreads) (&wcnt[0][0])[d] = 0;
-    goff[threadIdx.x] = offs[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
+    goff[threadIdx.x] = offs[(uint64_t)blockIdx.x * 256 + threadIdx.x];
     __syncthreads();
-    const uint64_t tbase = (uint64_t)blockIdx.x * kTile;
-    const uint32_t tcount = (uint32_t)(n - tbase < (uint64_t)kTile ? n - tbase : (uint64_t)kTile);
+    const uint64_t tbase = (uint64_t)blockIdx.x * kRTile;
+    const uint32_t tcount = (uint32_t)(n - tbase < (uint64_t)kRTile ? n - tbase : (uint64_t)kRTile);
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t key[kItems], val[kItems], rank[kItems];
+    uint32_t key[kRI], val[kRI], rank[kRI];
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
+    for (int it = 0; it < kRI; ++it) {
         const uint32_t li = (uint32_t)warp * kSub + it * 32 + lane;
         const bool ok = li < tcount;
-        key[it] = ok ? kin[tbase + li] : 0u;
-        val[it] = ok ? vin[tbase + li] : 0u;
-        const uint32_t d = ok ? ((key[it] >> shift) & 255u) : 256u;
+        key[it] = ok ? __ldg(kin + tbase + li) : 0u;
+        val[it] = ok ? __ldg(vin + tbase + li) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kRI; ++it) {
+        const uint32_t li = (uint32_t)warp * kSub + it * 32 + lane;
+        const uint32_t d = li < tcount ? ((key[it] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t base = d < 256u ? wcnt[warp][d] : 0u;
         rank[it] = base + __popc(peers & lt);
@@ -187,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) rs_scatter_k(const uint32_t *kin, co
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
+    for (int it = 0; it < kRI; ++it) {
         const uint32_t li = (uint32_t)warp * kSub + it * 32 + lane;
         if (li < tcount) {
             const uint32_t d = (key[it] >> shift) & 255u;
@@ -256,9 +338,9 @@ cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, uint64_t n, int6
 }
 
 size_t radix_scratch_elems(uint64_t n) {
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    const uint64_t hist = 256 * (ntiles ? ntiles : 1);
-    return (size_t)(hist + scan_scratch_elems(hist));
+    const uint64_t ntiles = (n + kRTile - 1) / kRTile;
+    const uint64_t nb = (ntiles + kScanTiles - 1) / kScanTiles;
+    return (size_t)(256 * ((ntiles ? ntiles : 1) + (nb ? nb : 1)));
 }
 
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
@@ -271,9 +353,10 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, u
         if (e != cudaSuccess) return e;
         return cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, s);
     }
-    const uint64_t ntiles = (n + kTile - 1) / kTile;
-    uint32_t *hist = scratch;
-    uint32_t *scan_tmp = scratch + 256 * ntiles;
+    const uint64_t ntiles = (n + kRTile - 1) / kRTile;
+    const uint64_t nb = (ntiles + kScanTiles - 1) / kScanTiles;
+    uint32_t *hist = scratch;                  // [ntiles][256]
+    uint32_t *part = scratch + 256 * ntiles;   // [nb][256]
     const uint32_t *ck = keys_in, *cv = vals_in;
     for (int p = 0; p < passes; ++p) {
         // The last pass must land in *_out: alternate backwards from it.
@@ -281,11 +364,11 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, u
         uint32_t *nk = to_out ? keys_out : tmp_k;
         uint32_t *nv = to_out ? vals_out : tmp_v;
         const int shift = 8 * p;
-        rs_hist_k<<<(unsigned)ntiles, kThreads, 0, s>>>(ck, n, shift, hist, (uint32_t)ntiles);
-        cudaError_t e = exclusive_scan_u32(hist, hist, 256 * ntiles, nullptr, scan_tmp, s);
-        if (e != cudaSuccess) return e;
-        rs_scatter_k<<<(unsigned)ntiles, kThreads, 0, s>>>(ck, cv, nk, nv, n, shift, hist,
-                                                           (uint32_t)ntiles);
+        rs_hist_k<<<(unsigned)ntiles, kThreads, 0, s>>>(ck, n, shift, hist);
+        rs_scan_a_k<<<(unsigned)nb, kThreads, 0, s>>>(hist, ntiles, part);
+        rs_scan_b_k<<<1, kThreads, 0, s>>>(part, nb);
+        rs_scan_c_k<<<(unsigned)nb, kThreads, 0, s>>>(hist, ntiles, part);
+        rs_scatter_k<<<(unsigned)ntiles, kThreads, 0, s>>>(ck, cv, nk, nv, n, shift, hist);
         ck = nk;
         cv = nv;
     }
