@@ -177,8 +177,9 @@ hm_status hm_autotune(hm_handle *h, void *cuda_stream, int32_t *config_out, doub
  *               (input numbering)
  *   count_out   HOST, may be NULL: |M|
  *   rounds_out  HOST, may be NULL: rounds that started with a live edge
- *   weight_out  HOST, may be NULL: w(M) summed in float64 in ascending edge
- *               id order (|M| for unweighted handles)
+ *   weight_out  HOST, may be NULL: w(M) = the exact sum of the matched
+ *               float32 weights (Sec. 2.1), rounded once to the nearest
+ *               float64, ties to even (|M| for unweighted handles)
  * Errors: HM_EINVAL (NULL handle, no match run yet), HM_ETIMEOUT (the round
  * cap stopped the loop; outputs then describe the partial matching),
  * HM_EINVAL with message "duplicate pin" if a round found no winner while
@@ -357,8 +358,8 @@ hm_status hm_batch_match(hm_batch *b, void *cuda_stream);
  *                at sum of counts_out[k] for k < i)
  *   counts_out   HOST int64[count] or NULL: |M_i|
  *   rounds_out   HOST int32[count] or NULL: rounds instance i takes alone
- *   weights_out  HOST double[count] or NULL: w(M_i), float64 in ascending id
- *                order (|M_i| when unweighted)
+ *   weights_out  HOST double[count] or NULL: w(M_i), the exact sum rounded
+ *                once to float64 as in hm_result (|M_i| when unweighted)
  * Errors: HM_EINVAL, HM_ETIMEOUT / HM_EINVAL / HM_ECUDA if a class's loop did
  * not finish cleanly (outputs are still written), HM_ECUDA.
  */

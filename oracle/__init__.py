@@ -12,6 +12,7 @@ function follows.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -188,10 +189,9 @@ def fmix32(x: int) -> int:
 
 
 def weight(h, in_matching) -> float:
-    """Matching weight: float64 sum in ascending edge-id order."""
+    """Matching weight w(M) = sum of w(e) over e in M (Sec. 2.1): the exact
+    sum of the float32 weights, rounded once to the nearest float64
+    (math.fsum is correctly rounded); |M| for unweighted input."""
     if h.weights is None:
         return float(int(np.count_nonzero(in_matching)))
-    acc = 0.0
-    for e in np.flatnonzero(in_matching):
-        acc += float(h.weights[e])
-    return acc
+    return math.fsum(float(x) for x in h.weights[np.asarray(in_matching, dtype=bool)])

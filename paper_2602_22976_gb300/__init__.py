@@ -125,7 +125,7 @@ class Result:
     edges: np.ndarray     # int32, ascending input edge ids of the matching
     count: int
     rounds: int
-    weight: float         # float64 sum in ascending edge-id order (|M| if unweighted)
+    weight: float         # exact sum of the weights, rounded once to float64 (|M| if unweighted)
     status: int           # HM_OK, or HM_ETIMEOUT when a round cap stopped the loop
 
     @property

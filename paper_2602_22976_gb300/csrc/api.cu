@@ -1,5 +1,6 @@
 // api.cu - the extern "C" entry points declared in include/hm.h.
 #include "hm_internal.cuh"
+#include "exact_sum.cuh"
 
 #include <climits>
 #include <cmath>
@@ -285,30 +286,21 @@ hm_status hm_result(hm_handle *hh, int32_t *edges_out, int64_t *count_out, int32
     if (st != HM_OK) return st;
     cudaStream_t s = h->cap_stream;
     const uint64_t m = (uint64_t)h->m;
-    cudaError_t e = compact_flags(h->inM, m, h->weighted ? h->weights : nullptr, h->res_idx, h->res_w,
-                                  h->res_part, s);
+    cudaError_t e = compact_flags(h->inM, m, nullptr, h->res_idx, nullptr, h->res_part, s);
+    const bool wsum = weight_out && h->weighted;
+    if (e == cudaSuccess && wsum) e = weight_buckets(h->inM, h->weights, m, h->res_bucket, h->sm_count, s);
     uint32_t count = 0;
+    uint64_t bucket[kExpBuckets];
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&count, h->res_part + compact_scratch_elems(m), sizeof count,
                             cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && wsum) e = cudaMemcpyAsync(bucket, h->res_bucket, sizeof bucket, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "result compaction");
     if (edges_out && count)
         if ((e = cudaMemcpy(edges_out, h->res_idx, (size_t)count * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "result copy");
-    if (weight_out) {
-        if (!h->weighted) {
-            *weight_out = (double)count;
-        } else {
-            std::vector<float> w(count);
-            if (count &&
-                (e = cudaMemcpy(w.data(), h->res_w, (size_t)count * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
-                return cuda_fail(e, "result weights");
-            double acc = 0.0;
-            for (uint32_t i = 0; i < count; ++i) acc += (double)w[i];  // ascending edge id
-            *weight_out = acc;
-        }
-    }
+    if (weight_out) *weight_out = wsum ? exact_sum_value(bucket) : (double)count;
     if (count_out) *count_out = count;
     if (rounds_out) *rounds_out = h->h_st->rounds_done;
     return loop_status(h);

@@ -13,6 +13,7 @@
 // in their latency-bound last rounds overlap the work of others. Each class
 // has its own launch shape, optionally picked by the autotuner.
 #include "hm_internal.cuh"
+#include "exact_sum.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -375,7 +376,7 @@ hm_status hm_batch_result(hm_batch *bb, int32_t *edges_out, int64_t *counts_out,
     if (e != cudaSuccess) return cuda_fail(e, "waiting for the batch");
     std::vector<int64_t> cnt(b->count, 0);
     std::vector<int32_t> rnd(b->count, 0);
-    std::vector<double> wsum(b->count, 0.0);
+    std::vector<ExactSum> wsum(b->weighted ? b->count : 0);
     std::vector<std::vector<int32_t>> per(b->count);
     hm_status worst = HM_OK;
     for (auto &c : b->cls) {
@@ -419,7 +420,7 @@ hm_status hm_batch_result(hm_batch *bb, int32_t *edges_out, int64_t *counts_out,
             per[i].push_back((int32_t)(g - c.mem[k].ub));
             cnt[i] += 1;
             rnd[i] = std::max(rnd[i], rr[t]);
-            wsum[i] += h->weighted ? (double)ww[t] : 1.0;
+            if (h->weighted) wsum[i].add(ww[t]);
         }
     }
     int64_t off = 0;
@@ -428,7 +429,7 @@ hm_status hm_batch_result(hm_batch *bb, int32_t *edges_out, int64_t *counts_out,
         off += cnt[i];
         if (counts_out) counts_out[i] = cnt[i];
         if (rounds_out) rounds_out[i] = rnd[i];
-        if (weights_out) weights_out[i] = wsum[i];
+        if (weights_out) weights_out[i] = b->weighted ? wsum[i].value() : (double)cnt[i];
     }
     return worst;
 }

@@ -192,6 +192,7 @@ struct Handle {
     int32_t *res_idx = nullptr;
     float *res_w = nullptr;
     uint32_t *res_part = nullptr;
+    unsigned long long *res_bucket = nullptr;  // [256] exponent buckets of the result weight
     uint64_t item_cap = 0, win_cap = 0;
     int64_t cap = 0;
     // graph
@@ -229,6 +230,10 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in,
 // w[i] into w_out when w != nullptr). part: compact_scratch_elems(n) + 1;
 // the count is left in part[compact_scratch_elems(n)].
 size_t compact_scratch_elems(uint64_t n);
+// bucket[E] (256 words, cleared here) <- sum of the integer significands of
+// w[i] over the flagged i with exponent field E (exact_sum.cuh rounds them).
+cudaError_t weight_buckets(const uint8_t *flags, const float *w, uint64_t n, unsigned long long *bucket,
+                           int sm_count, cudaStream_t s);
 cudaError_t compact_flags(const uint8_t *flags, uint64_t n, const float *w, int32_t *idx_out,
                           float *w_out, uint32_t *part, cudaStream_t s);
 

@@ -323,7 +323,34 @@ __global__ void __launch_bounds__(kThreads) cmp_write_k(const uint8_t *f, uint64
     }
 }
 
+// Per exponent field E, the sum of the integer significands of the weights
+// of the flagged entries (see exact_sum.cuh): block totals in shared memory,
+// one global atomic per block and bucket.
+__global__ void __launch_bounds__(kThreads) wsum_k(const uint8_t *__restrict__ f, const float *__restrict__ w,
+                                                   uint64_t n, unsigned long long *__restrict__ bucket) {
+    __shared__ unsigned long long sb[256];
+    sb[threadIdx.x] = 0;  // kThreads == 256
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)kThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kThreads) {
+        if (f[i]) {
+            const uint32_t u = __float_as_uint(w[i]);
+            const uint32_t E = (u >> 23) & 255u, fr = u & 0x7FFFFFu;
+            atomicAdd(&sb[E], (unsigned long long)(E ? (fr | 0x800000u) : fr));
+        }
+    }
+    __syncthreads();
+    if (sb[threadIdx.x]) atomicAdd(&bucket[threadIdx.x], sb[threadIdx.x]);
+}
+
 }  // namespace
+
+cudaError_t weight_buckets(const uint8_t *flags, const float *w, uint64_t n, unsigned long long *bucket,
+                           int sm_count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bucket, 0, 256 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    wsum_k<<<grid_for(n, kThreads, sm_count, 8), kThreads, 0, s>>>(flags, w, n, bucket);
+    return cudaGetLastError();
+}
 
 size_t scan_scratch_elems(uint64_t n) { return (size_t)((n + kTile - 1) / kTile) + 1; }
 

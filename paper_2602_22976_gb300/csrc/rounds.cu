@@ -788,6 +788,7 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     if ((st = dalloc(&h->res_idx, m, s, "result ids")) != HM_OK) return st;
     if ((st = dalloc(&h->res_w, m, s, "result weights")) != HM_OK) return st;
     if ((st = dalloc(&h->res_part, compact_scratch_elems(m) + 1, s, "result scratch")) != HM_OK) return st;
+    if ((st = dalloc(&h->res_bucket, 256, s, "result weight buckets")) != HM_OK) return st;
     cudaError_t e = cudaMemsetAsync(h->stats, 0, (size_t)kStatRounds * HM_STATS_COLS * sizeof(int64_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "stats reset");
     h->h_st = new (std::nothrow) DevState();
@@ -954,7 +955,7 @@ void free_handle_buffers(Handle *h) {
     free_rand_buffers(h);
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
                     h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win,
-                    h->items, h->inM, h->stats, h->st, h->res_idx, h->res_w, h->res_part};
+                    h->items, h->inM, h->stats, h->st, h->res_idx, h->res_w, h->res_part, h->res_bucket};
     cudaStream_t s = h->cap_stream;
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, s);

@@ -2,7 +2,7 @@
 
 The order on edges is strict, so the matching is unique: the matched edge
 set, the round count, the per-round winner counts and the matching weight
-(float64 sum in ascending id order on both sides) must be identical. The
+(the exact sum rounded once to float64, on both sides) must be identical. The
 per-vertex state after a capped run (T[v] of round r, or matched) must
 equal the oracle's state after r rounds.
 """

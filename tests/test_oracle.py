@@ -344,3 +344,28 @@ def test_randomised_mutant_caught():
     h = synth.small(seed=6)
     r = oracle.match(h, noise=100.0, mutant=6)
     assert oracle.check_local_max(h, r.in_matching, r.decided_round, noise=100.0) != -1
+
+
+def test_weight_is_the_exact_sum_rounded_once():
+    """w(M) = sum of w(e) over e in M (Sec. 2.1) is an exact real sum; the
+    oracle returns it rounded once to the nearest float64. Exact rational
+    arithmetic (fractions.Fraction, whose float() rounds correctly) fixes
+    that value independently, on weights from the generators' grid, over a
+    wide exponent range, and with subnormal and near-maximal float32
+    values, where a running float64 sum would drift."""
+    import types
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    special = np.array([2.0 ** -149, 1e-38, 1.0, 3.0e38, 0.1, 1.0 - 2.0 ** -24], dtype=np.float32)
+    for case in range(60):
+        m = int(rng.integers(1, 4000))
+        kind = case % 3
+        if kind == 0:
+            w = ((rng.integers(0, 1 << 24, m) + 1) * 2.0 ** -24).astype(np.float32)
+        elif kind == 1:
+            w = np.exp(rng.uniform(-85.0, 85.0, m)).astype(np.float32)
+        else:
+            w = rng.choice(special, m).astype(np.float32)
+        mask = rng.random(m) < 0.6
+        exact = sum((Fraction(float(x)) for x in w[mask]), Fraction(0))
+        assert oracle.weight(types.SimpleNamespace(weights=w), mask.astype(np.uint8)) == float(exact)
