@@ -48,6 +48,10 @@ WORKLOADS = {
                                                                               m=8_000_000 // sc),
                        sample=lambda seed: __import__("synth").unweighted(seed=seed, n=40_000, m=80_000)),
 }
+WORKLOADS["graph"] = dict(
+    desc="random geometric graph (DIMACS rgg class) n=2^23 avg degree 16, d=2, f32 w in (0,1]",
+    make=lambda seed, sc=1: __import__("synth").rgg(seed=seed, n=(1 << 23) // sc),
+    sample=lambda seed: __import__("synth").rgg(seed=seed, n=100_000))
 WORKLOADS["batch"] = dict(
     desc="4096 independent hypergraphs, n log-uniform in [100, 200000], m=2n, |e|~U{2..16}, f32 w",
     make=None, sample=lambda seed: __import__("synth").batch(64, seed=seed))

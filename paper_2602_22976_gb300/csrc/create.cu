@@ -178,6 +178,20 @@ __global__ void __launch_bounds__(kT) k_relabel(const int32_t *__restrict__ pins
     }
 }
 
+// d = 2: edge j's pins are the pair of input edge order[j]; eoffj[j] = 2j.
+__global__ void k_relabel_pairs(const int32_t *__restrict__ pins, const uint32_t *__restrict__ order, int64_t m,
+                                int64_t *__restrict__ eoffj, int32_t *__restrict__ pinsj, uint32_t *__restrict__ jval) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        eoffj[j] = 2 * j;
+        if (j == m) continue;
+        const int64_t e = order[j];
+        const int32_t a = __ldg(pins + 2 * e), b = __ldg(pins + 2 * e + 1);
+        reinterpret_cast<int2 *>(pinsj)[j] = make_int2(a, b);
+        reinterpret_cast<uint2 *>(jval)[j] = make_uint2((uint32_t)j, (uint32_t)j);
+    }
+}
+
 // voff from the vertex-sorted pin list: position i starts the segments of
 // the vertices (sv[i-1], sv[i]] (degree-0 vertices get empty segments).
 // firstj[v] = the first entry of v's list (or -2 for degree 0). Also flags a
@@ -321,6 +335,8 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
         return HM_EINVAL;
     }
     h->p16 = herr.max_size <= 0xFFFFull;
+    // sizes are >= 1 (validated), so kappa = 2m with none above 2 means all are 2
+    h->graph = m > 0 && herr.max_size == 2 && kappa == 2 * (uint64_t)m;
     cudaEventRecord(ev.e[1], s);
 
     // 2. order on edges: stable sort of ~priority over edges in id order
@@ -343,29 +359,36 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     cudaEventRecord(ev.e[2], s);
 
     // 3. edge CSR in j order
-    int64_t *szj = nullptr, *srcj = nullptr, *i64scratch = nullptr;
     if ((st = dalloc(&h->eoffj, (uint64_t)m + 1, s, "eoffj")) != HM_OK ||
-        (st = dalloc(&h->pinsj, kappa, s, "pinsj")) != HM_OK ||
-        (st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
-        (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
-        (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
+        (st = dalloc(&h->pinsj, kappa, s, "pinsj")) != HM_OK)
         return st;
-    k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj, srcj);
-    ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
-    tmp.drop(szj);
-    tmp.drop(i64scratch);
-    // val now receives j for every pin slot; the relabelled pins double as
-    // the keys of the vertex sort
-    {
-        const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;
-        int32_t *first = nullptr;
-        if ((st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK) return st;
-        k_tile_first<<<gm, kT, 0, s>>>(h->eoffj, m, ntiles, first);
-        if (ntiles > 0)
-            k_relabel<<<(unsigned)ntiles, kT, 0, s>>>(pins, srcj, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
-        tmp.drop(first);
-        tmp.drop(srcj);
+    if (h->graph) {
+        // d = 2: offsets 2j, each edge's pair gathered in one 8-byte load;
+        // val receives j for both pin slots (pinsj and val: 8-byte aligned)
+        k_relabel_pairs<<<gm, kT, 0, s>>>(pins, order_u, m, h->eoffj, h->pinsj, val);
+    } else {
+        int64_t *szj = nullptr, *srcj = nullptr, *i64scratch = nullptr;
+        if ((st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
+            (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
+            (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
+            return st;
+        k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj, srcj);
+        ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
+        tmp.drop(szj);
+        tmp.drop(i64scratch);
+        // val now receives j for every pin slot; the relabelled pins double as
+        // the keys of the vertex sort
+        {
+            const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;
+            int32_t *first = nullptr;
+            if ((st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK) return st;
+            k_tile_first<<<gm, kT, 0, s>>>(h->eoffj, m, ntiles, first);
+            if (ntiles > 0)
+                k_relabel<<<(unsigned)ntiles, kT, 0, s>>>(pins, srcj, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
+            tmp.drop(first);
+            tmp.drop(srcj);
+        }
     }
     cudaEventRecord(ev.e[3], s);
 

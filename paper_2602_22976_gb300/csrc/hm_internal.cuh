@@ -123,6 +123,7 @@ struct RoundArgs {
     int64_t m;
     int64_t cap;           // round cap
     int p16;               // P holds 16-bit counters, two per word
+    int graph;             // every edge has exactly two pins: edge j's pins are pinsj[2j], pinsj[2j + 1]
     uint64_t item_cap;     // capacity of items
     uint64_t win_cap;      // capacity of win
     cudaGraphConditionalHandle cond;
@@ -145,6 +146,7 @@ struct Handle {
     uint64_t kappa = 0;
     bool weighted = true;
     bool p16 = false;           // every edge has at most 65535 pins: 16-bit P counters
+    bool graph = false;         // every edge has exactly two pins (d = 2)
     uint64_t seed = 0;
     int sm_count = 0;
     // device buffers (owned)

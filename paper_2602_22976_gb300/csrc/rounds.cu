@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         if (i < a.m) {
             a.alive[i] = 1;
             a.inM[i] = 0;
-            if (!a.p16) {
+            if (a.graph) {  // every edge has two pins: no offsets to read
+                if ((i & 1) == 0) a.P[i >> 1] = i + 1 < a.m ? 0x00020002u : 2u;
+            } else if (!a.p16) {
                 a.P[i] = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
             } else if ((i & 1) == 0) {  // the word of edges i and i + 1
                 const uint32_t lo = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
@@ -217,8 +219,13 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
     uint32_t len = 0;
     int64_t b = 0;
     if (j >= 0) {
-        b = __ldg(a.eoffj + j);
-        len = (uint32_t)(__ldg(a.eoffj + j + 1) - b);
+        if (a.graph) {  // d = 2: the pins sit at 2j, 2j + 1
+            b = 2 * (int64_t)j;
+            len = 2;
+        } else {
+            b = __ldg(a.eoffj + j);
+            len = (uint32_t)(__ldg(a.eoffj + j + 1) - b);
+        }
         const int32_t ein = __ldg(a.order + j);
         a.inM[ein] = 1;
         a.wround[ein] = r;
@@ -752,6 +759,7 @@ RoundArgs round_args(const Handle *h) {
     a.m = h->m;
     a.cap = h->cap;
     a.p16 = h->p16 ? 1 : 0;
+    a.graph = h->graph ? 1 : 0;
     a.item_cap = h->item_cap;
     a.wround = h->wround;
     a.kill_chunk = h->cfg.kill_chunk;

@@ -108,7 +108,7 @@ __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
 // Proposal of a vertex for edge j (relabelled id) in round r: counts in the
 // round's buffer; returns whether it completed the count (j wins).
 __device__ __forceinline__ bool propose(const RoundArgs &a, uint32_t *Pc, int32_t j) {
-    const uint32_t size = (uint32_t)(a.eoffj[j + 1] - a.eoffj[j]);
+    const uint32_t size = a.graph ? 2u : (uint32_t)(a.eoffj[j + 1] - a.eoffj[j]);
     return atomicAdd(Pc + j, 1u) + 1u == size;
 }
 

@@ -22,6 +22,7 @@ tables in the appendix: heavy-tailed edge sizes and vertex degrees):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass, field
@@ -60,6 +61,8 @@ def _load():
         lib.synth_loguniform.restype = None
         lib.synth_arrivals.argtypes = [i64, f64, u64, p]
         lib.synth_arrivals.restype = None
+        lib.synth_rgg.argtypes = [i64, f64, u64, p, p]
+        lib.synth_rgg.restype = i64
         lib.synth_threads.argtypes = []
         lib.synth_threads.restype = i32
         _lib = lib
@@ -168,6 +171,31 @@ def from_edges(n: int, edges: list[list[int]], weights: list[float] | None,
     pins = np.array([v for e in edges for v in e], dtype=np.int32)
     w = None if weights is None else np.asarray(weights, dtype=np.float32)
     return Hypergraph(n, len(edges), eoff, pins, w, seed, name)
+
+
+def rgg(seed: int = 1, n: int = 1 << 23, avg_degree: float = 16.0) -> Hypergraph:
+    """Random geometric graph (every edge has two pins): n points uniform in
+    the unit square, an edge between points closer than r, with r chosen so
+    that the expected degree is avg_degree (n * pi * r^2); float32 weights
+    uniform on the 2^-24 grid of (0, 1]. The DIMACS rgg instances have
+    average degree about 16."""
+    lib = _load()
+    r = math.sqrt(avg_degree / (math.pi * max(n, 1)))
+    deg = np.empty(max(n, 1), dtype=np.int64)
+    m = lib.synth_rgg(n, r, seed, _ptr(deg), None)
+    if m < 0:
+        raise RuntimeError(f"synth_rgg failed ({m})")
+    off = np.zeros(max(n, 1), dtype=np.int64)
+    np.cumsum(deg[:-1], out=off[1:])
+    pins = np.empty(2 * max(int(m), 1), dtype=np.int32)
+    deg[:] = off
+    if lib.synth_rgg(n, r, seed, _ptr(deg), _ptr(pins)) != m:
+        raise RuntimeError("synth_rgg: second pass disagrees")
+    m = int(m)
+    eoff = np.arange(0, 2 * m + 1, 2, dtype=np.int64)
+    w = np.empty(max(m, 1), dtype=np.float32)
+    lib.synth_weights(m, seed, _ptr(w))
+    return Hypergraph(n, m, eoff, pins[:2 * m].copy(), w[:m].copy(), seed, f"rgg_n{n}_deg{avg_degree:g}")
 
 
 def threads() -> int:

@@ -37,7 +37,7 @@ static inline uint64_t sm_mix(uint64_t z)
 typedef struct { uint64_t s; } stream_t;
 
 /* purpose tags keep the size, pin, weight and shuffle streams apart */
-enum { P_SIZE = 1, P_PIN = 2, P_WEIGHT = 3, P_SHUFFLE = 4, P_BATCH = 5 };
+enum { P_SIZE = 1, P_PIN = 2, P_WEIGHT = 3, P_SHUFFLE = 4, P_BATCH = 5, P_POINT = 7 };
 
 static inline stream_t stream_for(uint64_t seed, uint64_t purpose, uint64_t idx)
 {
@@ -259,6 +259,115 @@ void synth_arrivals(int64_t count, double rate, uint64_t seed, double *t)
         acc += -log1p(-u) / rate;
         t[i] = acc;
     }
+}
+
+/* ---------------------------------------------------------- graphs (d = 2)
+ *
+ * Random geometric graph, the "rgg" class of the DIMACS graph instances the
+ * paper's graph experiments use: n points uniform in the unit square (point
+ * i draws its coordinates from its own stream), an edge {i, j} for every
+ * pair closer than `radius`. Points are bucketed in a grid of cells no
+ * smaller than the radius, so each point only looks at its 3 x 3 cell
+ * neighbourhood. Edges are listed by their smaller endpoint i ascending,
+ * then by the larger one, so the output does not depend on the thread
+ * count. Pass 1 (pins == NULL) fills deg[i] = edges {i, j} with j > i and
+ * returns their total; pass 2 writes the pairs at the prefix offsets. */
+static void rgg_point(uint64_t seed, int64_t i, double *x, double *y)
+{
+    stream_t r = stream_for(seed, P_POINT, (uint64_t)i);
+    *x = unit(&r);
+    *y = unit(&r);
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t synth_rgg(int64_t n, double radius, uint64_t seed, int64_t *deg, int32_t *pins)
+{
+    if (n < 0 || n > 0x7FFFFFFF || !(radius > 0.0) || !deg) return -1;
+    int64_t g = (int64_t)(1.0 / radius);
+    if (g < 1) g = 1;
+    if (g > 65536) g = 65536;
+    const int64_t cells = g * g;
+    double *px = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *py = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    int64_t *cstart = (int64_t *)calloc((size_t)cells + 1, sizeof(int64_t));
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    if (!px || !py || !cell || !cstart || !members) {
+        free(px); free(py); free(cell); free(cstart); free(members);
+        return -2;
+    }
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        rgg_point(seed, i, &px[i], &py[i]);
+        int64_t cx = (int64_t)(px[i] * (double)g), cy = (int64_t)(py[i] * (double)g);
+        if (cx >= g) cx = g - 1;
+        if (cy >= g) cy = g - 1;
+        cell[i] = cy * g + cx;
+    }
+    for (int64_t i = 0; i < n; ++i) cstart[cell[i] + 1]++;
+    for (int64_t c = 0; c < cells; ++c) cstart[c + 1] += cstart[c];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)cells);
+        if (!fill) {
+            free(px); free(py); free(cell); free(cstart); free(members);
+            return -2;
+        }
+        memcpy(fill, cstart, sizeof(int64_t) * (size_t)cells);
+        for (int64_t i = 0; i < n; ++i) members[fill[cell[i]]++] = i; /* ascending i per cell */
+        free(fill);
+    }
+    const double r2 = radius * radius;
+    int64_t total = 0;
+    int err = 0;
+    #pragma omp parallel for schedule(dynamic, 4096) reduction(+ : total)
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t cx = cell[i] % g, cy = cell[i] / g;
+        int64_t nb[64];
+        int64_t k = 0;
+        int64_t base = pins ? deg[i] : 0; /* pass 2: deg holds the offsets */
+        for (int64_t dy = -1; dy <= 1; ++dy) {
+            for (int64_t dx = -1; dx <= 1; ++dx) {
+                const int64_t x = cx + dx, y = cy + dy;
+                if (x < 0 || y < 0 || x >= g || y >= g) continue;
+                const int64_t c = y * g + x;
+                for (int64_t t = cstart[c]; t < cstart[c + 1]; ++t) {
+                    const int64_t j = members[t];
+                    if (j <= i) continue;
+                    const double ddx = px[i] - px[j], ddy = py[i] - py[j];
+                    if (ddx * ddx + ddy * ddy < r2) {
+                        if (!pins) {
+                            ++k;
+                        } else if (k < 64) {
+                            nb[k++] = j;
+                        } else {
+                            ++k; /* more than 64 larger neighbours: not expected at these radii */
+                        }
+                    }
+                }
+            }
+        }
+        if (!pins) {
+            deg[i] = k;
+            total += k;
+        } else if (k > 64) {
+            #pragma omp atomic write
+            err = 1;
+        } else {
+            qsort(nb, (size_t)k, sizeof(int64_t), cmp_i64);
+            for (int64_t q = 0; q < k; ++q) {
+                pins[2 * (base + q)] = (int32_t)i;
+                pins[2 * (base + q) + 1] = (int32_t)nb[q];
+            }
+            total += k;
+        }
+    }
+    free(px); free(py); free(cell); free(cstart); free(members);
+    return err ? -3 : total;
 }
 
 int synth_threads(void)

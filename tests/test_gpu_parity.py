@@ -75,6 +75,12 @@ def test_powerlaw_scaled(seed):
     assert_parity(synth.large(seed=seed, n=1_000_000, m=2_000_000))
 
 
+@pytest.mark.parametrize("n,deg", [(30_000, 16.0), (50_000, 4.0), (20_000, 40.0)])
+def test_graph_rgg(n, deg):
+    """Graphs (d = 2): random geometric graphs of the DIMACS rgg class."""
+    assert_parity(synth.rgg(seed=3, n=n, avg_degree=deg))
+
+
 def test_unweighted_scaled():
     assert_parity(synth.unweighted(seed=1, n=400_000, m=800_000))
     assert_parity(synth.unweighted(seed=7, n=10_000, m=20_000))

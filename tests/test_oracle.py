@@ -108,9 +108,10 @@ def _instances():
     yield synth.unweighted(seed=4, n=20_000, m=40_000)
     yield synth.large(seed=5, n=20_000, m=40_000, kmax=256)
     yield synth.generate(50, 4000, kmin=2, kmax=4, seed=6)  # dense: many ties in the argmax
+    yield synth.rgg(seed=7, n=5_000)  # a graph (every edge has two pins)
 
 
-@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("idx", range(7))
 def test_definitions_and_greedy(idx):
     h = list(_instances())[idx]
     r = oracle.match(h)
