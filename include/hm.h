@@ -60,6 +60,8 @@ typedef enum {
 #define HM_BORROW_INPUT 0x2u  /* accepted for compatibility: inputs are never kept (see hm_create) */
 #define HM_VALIDATE     0x4u  /* accepted for compatibility: full validation always runs */
 #define HM_AUTOTUNE     0x8u  /* hm_batch_create: autotune every size class's launch shape */
+#define HM_ONE_CLASS    0x10u /* hm_batch_create: one size class for all instances (one union, one
+                                 build: less setup for small batches; the result is the same) */
 
 /*
  * hm_create - build a matching handle for one hypergraph.
@@ -332,7 +334,7 @@ hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff, const int3
  *            hm_create (starting at 0), concatenated in instance order
  *   pins     DEVICE int32[sum(kappa_i)]: instance-local vertex ids, concatenated
  *   weights  DEVICE float32[sum(m[i])], concatenated; NULL with HM_UNWEIGHTED
- *   seed, flags  as hm_create, plus HM_AUTOTUNE
+ *   seed, flags  as hm_create, plus HM_AUTOTUNE and HM_ONE_CLASS
  * Instances are grouped into size classes by kappa (factors of four); each
  * class is matched as the disjoint union of its instances, and all classes
  * are independent branches of one CUDA graph. Every instance gets exactly
@@ -377,13 +379,16 @@ void hm_batch_destroy(hm_batch *b);
 /*
  * hm_server_create - a request loop with continuous batching (no
  * counterpart in the paper). `slots` worker threads, each with its own CUDA
- * stream on the current device, take requests from a FIFO queue; the queue
- * head is admitted as soon as a slot is free and its estimated device
- * footprint (36*kappa + 64*m + 72*n bytes + 16 MiB) fits under the budget:
+ * stream on the current device, take requests from a FIFO queue. A free
+ * worker admits the queue head and the requests queued right behind it
+ * that are compatible (same flags; for HM_UNWEIGHTED the same seed), up to
+ * 256 requests and 2^26 pins, as long as their estimated device footprints
+ * (36*kappa + 64*m + 72*n bytes + 16 MiB each) fit under the budget:
  * `hbm_budget_bytes`, capped at 90 % of the free device memory at creation
- * (0 = that cap). Admitted requests run the hm_solve_host path on their
- * worker's stream, so requests arriving while others are on the GPU overlap
- * with them, and each gets the same result as alone.
+ * (0 = that cap). A lone request runs the hm_solve_host path on the
+ * worker's stream; a group runs as one batch (hm_batch_create with
+ * HM_ONE_CLASS, one match). Requests arriving while others are on the GPU
+ * overlap with them, and each gets the same result as alone.
  * Errors: HM_EINVAL (slots outside [1, 256]), HM_ENOMEM, HM_ECUDA.
  */
 hm_status hm_server_create(hm_server **out, int32_t slots, uint64_t hbm_budget_bytes);
@@ -408,8 +413,9 @@ hm_status hm_server_submit(hm_server *s, int64_t n, int64_t m, const int64_t *eo
 hm_status hm_server_wait(hm_server *s, int64_t ticket, int32_t *edges_out, int64_t *count_out,
                          int32_t *rounds_out, double *weight_out, double *latency_ms_out);
 
-/* hm_server_stats - HOST int64[7]: completed, queued, in flight, peak in
- * flight, reserved bytes, peak reserved bytes, budget. Errors: HM_EINVAL. */
+/* hm_server_stats - HOST int64[9]: completed, queued, in flight, peak in
+ * flight, reserved bytes, peak reserved bytes, budget, units of work started
+ * (single requests or groups), largest group. Errors: HM_EINVAL. */
 hm_status hm_server_stats(hm_server *s, int64_t *stats_out);
 
 /* hm_server_destroy - finish every submitted request, stop the workers and

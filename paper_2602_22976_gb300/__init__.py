@@ -24,7 +24,7 @@ from . import build as _build
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ECUDA, HM_ETIMEOUT, HM_EBUSY = range(6)
 STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "HM_ETIMEOUT",
                 5: "HM_EBUSY"}
-HM_UNWEIGHTED, HM_BORROW_INPUT, HM_VALIDATE, HM_AUTOTUNE = 0x1, 0x2, 0x4, 0x8
+HM_UNWEIGHTED, HM_BORROW_INPUT, HM_VALIDATE, HM_AUTOTUNE, HM_ONE_CLASS = 0x1, 0x2, 0x4, 0x8, 0x10
 HM_VERTEX_MATCHED, HM_VERTEX_NONE = -1, -2
 STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills", "items", "next", "live")
 KERNELS = ("init", "argmax", "win", "kill", "round_end")
@@ -262,7 +262,7 @@ class Batch:
     unweighted, one seed). Inputs are concatenated and copied to the device.
     """
 
-    def __init__(self, hgs, autotune: bool = False, stream=None, device: str = "cuda"):
+    def __init__(self, hgs, autotune: bool = False, stream=None, device: str = "cuda", one_class: bool = False):
         import torch
         self._b = None
         self.count = len(hgs)
@@ -277,7 +277,8 @@ class Batch:
         if weighted:
             w = torch.from_numpy(np.concatenate([np.asarray(h.weights, np.float32) for h in hgs])).to(device)
         torch.cuda.current_stream().synchronize()
-        flags = (0 if weighted else HM_UNWEIGHTED) | (HM_AUTOTUNE if autotune else 0)
+        flags = ((0 if weighted else HM_UNWEIGHTED) | (HM_AUTOTUNE if autotune else 0)
+                 | (HM_ONE_CLASS if one_class else 0))
         b = ctypes.c_void_p()
         st = lib().hm_batch_create(ctypes.byref(b), self.count, self.n.ctypes.data, self.m.ctypes.data,
                                    eoff.data_ptr(), pins.data_ptr() if pins.numel() else None,
@@ -335,7 +336,7 @@ class Batch:
 
 
 SERVER_STATS = ("completed", "queued", "inflight", "peak_inflight", "reserved_bytes",
-                "peak_reserved_bytes", "budget_bytes")
+                "peak_reserved_bytes", "budget_bytes", "groups", "peak_group")
 
 
 class Server:

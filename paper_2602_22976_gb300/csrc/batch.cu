@@ -33,6 +33,7 @@ struct Member {            // one instance inside its class's union
     int64_t pbase;         // first pin in the caller's pins array
     int64_t wbase;         // first weight in the caller's weights array
     int64_t ub, upb, vb;   // first union edge, union pin, union vertex
+    int64_t nv;            // its vertex count: local pins must be in [0, nv)
 };
 
 struct BatchClass {
@@ -55,10 +56,13 @@ struct Batch {
 };
 
 // kappa of every instance: its last offset
+// first and last offset of every instance: out[2i] = eoff[first], out[2i+1] = eoff[last]
 __global__ void k_last_offsets(const int64_t *__restrict__ eoff, const int64_t *__restrict__ last_idx,
-                               int32_t count, int64_t *__restrict__ out) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-        out[i] = eoff[last_idx[i]];
+                               const int64_t *__restrict__ m, int32_t count, int64_t *__restrict__ out) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        out[2 * i] = eoff[last_idx[i] - m[i]];
+        out[2 * i + 1] = eoff[last_idx[i]];
+    }
 }
 
 __device__ __forceinline__ int member_of(const int64_t *base, int nmem, int64_t x) {
@@ -88,14 +92,17 @@ __global__ void k_union_edges(const int64_t *__restrict__ eoff, const float *__r
     }
 }
 
-// union pins (thread per union pin)
+// union pins (thread per union pin). A pin outside its own instance's
+// [0, n) becomes -1, which the union's validation rejects: offset into the
+// union it would otherwise land on another instance's vertex.
 __global__ void k_union_pins(const int32_t *__restrict__ pins, const Member *__restrict__ mem,
                              const int64_t *__restrict__ pbase_u, int nmem, uint64_t kappa_u,
                              int32_t *__restrict__ pins_u) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < kappa_u;
          p += (uint64_t)gridDim.x * blockDim.x) {
         const Member mb = mem[member_of(pbase_u, nmem, (int64_t)p)];
-        pins_u[p] = (int32_t)(pins[mb.pbase + ((int64_t)p - mb.upb)] + mb.vb);
+        const int64_t lp = pins[mb.pbase + ((int64_t)p - mb.upb)];
+        pins_u[p] = (lp < 0 || lp >= mb.nv) ? -1 : (int32_t)(lp + mb.vb);
     }
 }
 
@@ -236,7 +243,8 @@ hm_status hm_batch_create(hm_batch **out, int32_t count, const int64_t *n, const
     *out = nullptr;
     if (count < 1) return bad("count must be >= 1");
     if (!n || !m) return bad("n and m (host arrays) must not be NULL");
-    if (flags & ~(HM_UNWEIGHTED | HM_BORROW_INPUT | HM_VALIDATE | HM_AUTOTUNE)) return bad("unknown flag bits");
+    if (flags & ~(HM_UNWEIGHTED | HM_BORROW_INPUT | HM_VALIDATE | HM_AUTOTUNE | HM_ONE_CLASS))
+        return bad("unknown flag bits");
     if (!eoff) return bad("eoff is NULL");
     const bool weighted = !(flags & HM_UNWEIGHTED);
     int64_t sum_m = 0;
@@ -266,17 +274,28 @@ hm_status hm_batch_create(hm_batch **out, int32_t count, const int64_t *n, const
         last[i] = ei + m[i];
         ei += m[i] + 1;
     }
-    int64_t *d_last = nullptr, *d_kappa = nullptr;
+    int64_t *d_last = nullptr, *d_m = nullptr, *d_kappa = nullptr;
+    std::vector<int64_t> ends(2 * (size_t)count);
     hm_status st = upload(&d_last, last, s);
-    if (st == HM_OK && (e = cudaMallocAsync((void **)&d_kappa, (size_t)count * 8, s)) != cudaSuccess)
+    if (st == HM_OK) st = upload(&d_m, b->m, s);
+    if (st == HM_OK && (e = cudaMallocAsync((void **)&d_kappa, (size_t)count * 16, s)) != cudaSuccess)
         st = cuda_fail(e, "batch kappa");
     if (st == HM_OK) {
-        k_last_offsets<<<grid_for((uint64_t)count, kBT, sm_count, 8), kBT, 0, s>>>(eoff, d_last, count, d_kappa);
-        if ((e = cudaMemcpyAsync(b->kappa.data(), d_kappa, (size_t)count * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        k_last_offsets<<<grid_for((uint64_t)count, kBT, sm_count, 8), kBT, 0, s>>>(eoff, d_last, d_m, count, d_kappa);
+        if ((e = cudaMemcpyAsync(ends.data(), d_kappa, (size_t)count * 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             st = cuda_fail(e, "batch kappa");
     }
+    for (int32_t i = 0; i < count && st == HM_OK; ++i) {
+        if (ends[2 * (size_t)i] != 0) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "instance %d: eoff[0] must be 0", (int)i);
+            st = bad(buf);
+        }
+        b->kappa[i] = ends[2 * (size_t)i + 1];
+    }
     if (d_last) cudaFreeAsync(d_last, s);
+    if (d_m) cudaFreeAsync(d_m, s);
     if (d_kappa) cudaFreeAsync(d_kappa, s);
     if (st != HM_OK) {
         free_batch(b);
@@ -295,10 +314,12 @@ hm_status hm_batch_create(hm_batch **out, int32_t count, const int64_t *n, const
         mem[i].eidx = eidx[i];
         mem[i].pbase = pb;
         mem[i].wbase = wb;
+        mem[i].nv = n[i];
         pb += b->kappa[i];
         wb += m[i];
         int cl = 0;
-        for (int64_t k = b->kappa[i]; k >= 4; k >>= 2) ++cl;
+        if (!(flags & HM_ONE_CLASS))
+            for (int64_t k = b->kappa[i]; k >= 4; k >>= 2) ++cl;
         b->cls_of[i] = cl;
         maxc = std::max(maxc, cl);
     }

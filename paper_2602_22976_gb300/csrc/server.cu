@@ -3,13 +3,18 @@
 // setting of hypergraphs arriving inside a larger computation, Sec. 5.1).
 //
 // Requests (host edge CSR) enter a FIFO queue. `slots` worker threads, each
-// with its own CUDA stream, admit the queue head as soon as a slot is free
-// and its estimated device footprint fits under the HBM budget, and run it
-// through the public single-instance path (upload, hm_create, hm_match,
-// hm_result) on their stream. Requests that arrive while others are on the
-// GPU are admitted as slots and memory free up and their kernels run
-// concurrently with the others'. Every request is matched by the same code
-// as when it is alone, so its result does not depend on the mix.
+// with its own CUDA stream, admit work as soon as a slot is free and its
+// estimated device footprint fits under the HBM budget. A free worker takes
+// the queue head and every compatible request queued right behind it (up
+// to kGroupMax requests and kGroupPins pins, within the budget): a lone
+// request runs the public single-instance path (upload, hm_create,
+// hm_match, hm_result); a group runs as one batch (one upload into
+// concatenated buffers, hm_batch_create with all instances in one union,
+// one graph launch, hm_batch_result), so under load the per-request setup
+// is paid once per group. Requests that arrive while others are on the GPU
+// are admitted as slots and memory free up, and their kernels run
+// concurrently with the others'. Batched instances are disjoint inside the
+// union, so every request gets exactly the result it gets alone.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -55,6 +60,7 @@ struct Server {
     uint64_t budget = 0;
     uint64_t reserved = 0, peak_reserved = 0;
     int64_t inflight = 0, peak_inflight = 0, done_count = 0;
+    int64_t groups = 0, peak_group = 0;  // units of work started, largest group
     int64_t next_ticket = 1;
     bool stop = false;
     std::mutex mu;
@@ -64,10 +70,94 @@ struct Server {
     std::vector<std::thread> workers;
 };
 
+constexpr size_t kGroupMax = 256;              // requests per group
+constexpr uint64_t kGroupPins = 64ull << 20;   // pins per group
+
 // Device bytes one request may hold at its peak (hm_create temporaries plus
 // the handle and the uploaded input), with slack for allocator rounding.
 uint64_t footprint(int64_t n, int64_t m, uint64_t kappa) {
     return 36 * kappa + 64 * (uint64_t)m + 72 * (uint64_t)n + (16ull << 20);
+}
+
+// Requests that can share one batch: the same flags, and for unweighted
+// input the same seed (its hash priorities depend on the seed; the
+// weighted order depends on the weights and local edge ids only).
+bool compatible(const Request &a, const Request &b) {
+    if (a.flags != b.flags) return false;
+    return !(a.flags & HM_UNWEIGHTED) || a.seed == b.seed;
+}
+
+void solve_alone(Request &r, cudaStream_t s) {
+    r.edges.resize((size_t)std::max<int64_t>(r.m, 1));
+    r.status = hm_solve_host(r.n, r.m, r.eoff, r.pins, r.w, r.seed, r.flags, r.edges.data(), &r.count, &r.rounds,
+                             &r.weight, s);
+    if (r.status != HM_OK) r.err = hm_last_error();
+    r.edges.resize(r.status == HM_OK ? (size_t)r.count : 0);
+}
+
+// A group as one batch. If anything fails (an invalid request among them,
+// say), every request of the group runs alone, so each reports its own
+// status.
+void solve_group(std::vector<std::shared_ptr<Request>> &g, cudaStream_t s) {
+    const int32_t cnt = (int32_t)g.size();
+    std::vector<int64_t> n(cnt), m(cnt);
+    uint64_t E = 0, K = 0, M = 0;
+    for (int32_t i = 0; i < cnt; ++i) {
+        n[i] = g[i]->n;
+        m[i] = g[i]->m;
+        E += (uint64_t)g[i]->m + 1;
+        K += g[i]->kappa;
+        M += (uint64_t)g[i]->m;
+    }
+    const bool weighted = !(g[0]->flags & HM_UNWEIGHTED);
+    int64_t *d_eoff = nullptr;
+    int32_t *d_pins = nullptr;
+    float *d_w = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_eoff, E * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_pins, std::max<uint64_t>(K, 1) * 4, s);
+    if (e == cudaSuccess && weighted) e = cudaMallocAsync((void **)&d_w, std::max<uint64_t>(M, 1) * 4, s);
+    uint64_t eo = 0, po = 0, wo = 0;
+    for (int32_t i = 0; i < cnt && e == cudaSuccess; ++i) {
+        const Request &r = *g[i];
+        e = cudaMemcpyAsync(d_eoff + eo, r.eoff, ((size_t)r.m + 1) * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && r.kappa)
+            e = cudaMemcpyAsync(d_pins + po, r.pins, (size_t)r.kappa * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && weighted && r.m)
+            e = cudaMemcpyAsync(d_w + wo, r.w, (size_t)r.m * 4, cudaMemcpyHostToDevice, s);
+        eo += (uint64_t)r.m + 1;
+        po += r.kappa;
+        wo += (uint64_t)r.m;
+    }
+    hm_status st = e == cudaSuccess ? HM_OK : HM_ECUDA;
+    if (e != cudaSuccess) cudaGetLastError();
+    hm_batch *b = nullptr;
+    if (st == HM_OK)
+        st = hm_batch_create(&b, cnt, n.data(), m.data(), d_eoff, d_pins, d_w, g[0]->seed,
+                             g[0]->flags | HM_ONE_CLASS, s);
+    if (d_eoff) cudaFreeAsync(d_eoff, s);
+    if (d_pins) cudaFreeAsync(d_pins, s);
+    if (d_w) cudaFreeAsync(d_w, s);
+    std::vector<int32_t> edges((size_t)std::max<uint64_t>(M, 1));
+    std::vector<int64_t> counts(cnt, 0);
+    std::vector<int32_t> rounds(cnt, 0);
+    std::vector<double> weights(cnt, 0.0);
+    if (st == HM_OK) st = hm_batch_match(b, s);
+    if (st == HM_OK) st = hm_batch_result(b, edges.data(), counts.data(), rounds.data(), weights.data());
+    hm_batch_destroy(b);
+    if (st != HM_OK) {
+        for (auto &r : g) solve_alone(*r, s);
+        return;
+    }
+    size_t off = 0;
+    for (int32_t i = 0; i < cnt; ++i) {
+        Request &r = *g[i];
+        r.edges.assign(edges.begin() + (ptrdiff_t)off, edges.begin() + (ptrdiff_t)(off + (size_t)counts[i]));
+        off += (size_t)counts[i];
+        r.count = counts[i];
+        r.rounds = rounds[i];
+        r.weight = weights[i];
+        r.status = HM_OK;
+    }
 }
 
 void worker(Server *S) {
@@ -75,33 +165,50 @@ void worker(Server *S) {
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (;;) {
-        std::shared_ptr<Request> r;
+        std::vector<std::shared_ptr<Request>> g;
+        uint64_t bytes = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] {
                 return S->stop || (!S->queue.empty() && S->reserved + S->queue.front()->bytes <= S->budget);
             });
             if (S->stop) break;
-            r = S->queue.front();
+            g.push_back(S->queue.front());
             S->queue.pop_front();
-            S->reserved += r->bytes;
+            bytes = g[0]->bytes;
+            uint64_t pins = g[0]->kappa;
+            // the compatible requests queued right behind the head (FIFO order kept)
+            while (!S->queue.empty() && g.size() < kGroupMax) {
+                const std::shared_ptr<Request> &q = S->queue.front();
+                if (!compatible(*g[0], *q) || pins + q->kappa > kGroupPins ||
+                    S->reserved + bytes + q->bytes > S->budget)
+                    break;
+                bytes += q->bytes;
+                pins += q->kappa;
+                g.push_back(q);
+                S->queue.pop_front();
+            }
+            S->reserved += bytes;
             S->peak_reserved = std::max(S->peak_reserved, S->reserved);
-            S->inflight += 1;
+            S->inflight += (int64_t)g.size();
             S->peak_inflight = std::max(S->peak_inflight, S->inflight);
+            S->groups += 1;
+            S->peak_group = std::max<int64_t>(S->peak_group, (int64_t)g.size());
         }
-        r->t_start = Clock::now();
-        r->edges.resize((size_t)std::max<int64_t>(r->m, 1));
-        r->status = hm_solve_host(r->n, r->m, r->eoff, r->pins, r->w, r->seed, r->flags, r->edges.data(),
-                                  &r->count, &r->rounds, &r->weight, s);
-        if (r->status != HM_OK) r->err = hm_last_error();
-        r->edges.resize((size_t)r->count);
+        const Clock::time_point t0 = Clock::now();
+        for (auto &r : g) r->t_start = t0;
+        if (g.size() == 1) solve_alone(*g[0], s);
+        else solve_group(g, s);
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            r->t_done = Clock::now();
-            r->done = true;
-            S->reserved -= r->bytes;
-            S->inflight -= 1;
-            S->done_count += 1;
+            const Clock::time_point t1 = Clock::now();
+            for (auto &r : g) {
+                r->t_done = t1;
+                r->done = true;
+            }
+            S->reserved -= bytes;
+            S->inflight -= (int64_t)g.size();
+            S->done_count += (int64_t)g.size();
         }
         S->cv_done.notify_all();
         S->cv_work.notify_all();  // memory was released: the queue head may fit now
@@ -226,6 +333,8 @@ hm_status hm_server_stats(hm_server *ss, int64_t *stats_out) {
     stats_out[4] = (int64_t)S->reserved;
     stats_out[5] = (int64_t)S->peak_reserved;
     stats_out[6] = (int64_t)S->budget;
+    stats_out[7] = S->groups;
+    stats_out[8] = S->peak_group;
     return HM_OK;
 }
 

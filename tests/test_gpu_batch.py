@@ -59,6 +59,17 @@ def test_batch_matches_solo_oracle(weighted):
         check_against_oracle(hs, b.result())
 
 
+@pytest.mark.parametrize("weighted", [True, False])
+def test_batch_one_class(weighted):
+    """HM_ONE_CLASS: every instance in one union; each still gets its solo result."""
+    hs = mixed_instances(5 if weighted else 6, weighted, count=30)
+    with hmlib.Batch(hs, one_class=True) as b:
+        ncls, cls, cfg = b.info()
+        assert ncls == 1 and np.all(cls == 0)
+        b.match()
+        check_against_oracle(hs, b.result())
+
+
 def test_batch_degenerate_members():
     hs = [synth.from_edges(5, [], []),
           synth.from_edges(3, [[0, 1, 2]], [0.5]),
@@ -98,3 +109,26 @@ def test_single_handle_autotune_and_config():
         assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
         with pytest.raises(hmlib.HMError):
             mt.launch_config((8, 0, 0, 0))
+
+
+def test_batch_rejects_cross_instance_inputs():
+    """Inside the union a pin of one instance would be another instance's
+    vertex, so pins are checked against their own instance's n; and every
+    instance's offsets must start at 0 (else its first edges would take the
+    previous instance's pins)."""
+    a = synth.small(seed=3, n=400, m=800)
+    b = synth.small(seed=4, n=400, m=800)
+    for h in (a, b):
+        h.seed = 1
+    bad_pin = synth.Hypergraph(b.n, b.m, b.eoff.copy(), b.pins.copy(), b.weights, 1, "bad pin")
+    bad_pin.pins[10] = b.n + 3  # inside the union, outside its own instance
+    with pytest.raises(hmlib.HMError) as ei:
+        hmlib.Batch([a, bad_pin])
+    assert ei.value.status == hmlib.HM_EINVAL
+    shifted = synth.Hypergraph(b.n, b.m - 1, b.eoff[1:].copy(), b.pins, b.weights[1:].copy(), 1, "offsets from 2")
+    with pytest.raises(hmlib.HMError) as ei:
+        hmlib.Batch([a, shifted])
+    assert ei.value.status == hmlib.HM_EINVAL
+    with hmlib.Batch([a, b]) as ok:  # the valid pair still works
+        ok.match()
+        check_against_oracle([a, b], ok.result())

@@ -91,3 +91,45 @@ def test_refusals():
     import ctypes
     s = ctypes.c_void_p()
     assert L.hm_server_create(ctypes.byref(s), 0, 0) == hmlib.HM_EINVAL
+
+
+def test_queued_requests_are_grouped():
+    """With one slot and a full queue, compatible requests queued behind the
+    head run as one batch; each still gets its solo result, and unweighted
+    requests group only with the same seed."""
+    rng = np.random.default_rng(9)
+    hs = []
+    for i in range(24):
+        h = synth.serve_request(int(np.exp(rng.uniform(np.log(1e3), np.log(2e5)))), seed=900 + i)
+        if i >= 16:
+            h.weights = None
+            h.seed = 77 if i < 20 else 78  # two seeds: two unweighted groups
+        hs.append(h)
+    with hmlib.Server(slots=1) as srv:
+        tickets = [srv.submit(h) for h in hs]
+        got = [srv.wait(t)[0] for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(hs)
+    assert st["peak_group"] >= 2 and st["groups"] < len(hs)
+    for h, r in zip(hs, got):
+        o = oracle.match(h)
+        assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+        assert r.weight == oracle.weight(h, o.in_matching)
+
+
+def test_invalid_request_inside_a_group():
+    """A request with a pin outside [0, n) fails on the device; its group then
+    runs request by request, so only that request reports HM_EINVAL."""
+    hs = [synth.serve_request(20_000, seed=300 + i) for i in range(6)]
+    bad = hs[3]
+    bad.pins = bad.pins.copy()
+    bad.pins[5] = bad.n + 7
+    with hmlib.Server(slots=1) as srv:
+        tickets = [srv.submit(h) for h in hs]
+        got = [srv.wait(t, allow=(hmlib.HM_OK, hmlib.HM_EINVAL))[0] for t in tickets]
+    for i, (h, r) in enumerate(zip(hs, got)):
+        if i == 3:
+            assert r.status == hmlib.HM_EINVAL
+        else:
+            o = oracle.match(h)
+            assert r.status == hmlib.HM_OK and np.array_equal(r.edges, o.edges)
