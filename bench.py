@@ -163,14 +163,18 @@ class Clocks:
                 "power_w_max": max(power) if power else None}
 
 
-def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool = False) -> dict:
+def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool = False,
+                 p16: bool = True) -> dict:
     """Algorithmic bytes per kernel kind, summed over rounds (per-unit figures
-    in the design doc, section 6), from the per-round counters of hm_round_stats."""
+    in the design doc, section 6), from the per-round counters of hm_round_stats.
+    p16: the fixed order's P counters are 16 bits wide (every edge has at
+    most 65535 pins)."""
     ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT, LIVE = range(9)
+    pc = 2 if p16 else 4  # bytes of one P counter
     if random:  # flags, two counter buffers, mask; records, offsets; list copy
         init = float(m * (1 + 4 + 4 + 1) + n * (16 + 16) + kappa * 8)
-    else:
-        init = float(m * (1 + 8 + 4 + 1) + n * (4 + 8))
+    else:       # flag, mask, P copied from its initial copy (read + write)
+        init = float(m * (1 + 1 + 2 * pc))
     b = {"init": init, "argmax": 0.0, "win": 0.0, "kill": 0.0, "round_end": 0.0}
     for r, row in enumerate(stats):
         row = row.astype(np.float64)
@@ -184,12 +188,13 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
                             + row[LIVE] * (8 + 4) + row[PROP] * (16 + 4 + 16 + 8 + 4)
                             + row[NEXT] * 4)
         else:
-            if r == 0:  # record read; proposal = P read+write; kept vertex = list write
-                b["argmax"] += row[ACT] * 16 + row[PROP] * 8 + row[NEXT] * 4
+            if r == 0:  # first entry read + record (T, cursor) write; proposal =
+                        # P read+write; kept vertex = list write
+                b["argmax"] += row[ACT] * (4 + 8) + row[PROP] * 2 * pc + row[NEXT] * 4
             else:       # list + record + live flag; skipped entry = entry + flag;
                         # proposal = record write + P read+write; kept vertex = list write
                 b["argmax"] += (row[ACT] * (4 + 16 + 1) + row[ADV] * (4 + 1)
-                                + row[PROP] * (8 + 8) + row[NEXT] * 4)
+                                + row[PROP] * (8 + 2 * pc) + row[NEXT] * 4)
             b["argmax"] += row[WIN] * (4 + 4 + 4)  # winner staged, read, listed
         b["win"] += winb + row[WIN] * 4  # the winner list
         # kill range read; killed entry: entry + flag
@@ -515,7 +520,8 @@ def run_ours(args, world, rank, local):
     prof = mt.profile(stream)
     stats = mt.round_stats()
     create_ms = mt.create_ms()
-    kb = kernel_bytes(stats, h.n, h.m, h.kappa, rnd_mode)
+    max_size = int(np.diff(h.eoff).max()) if h.m else 0
+    kb = kernel_bytes(stats, h.n, h.m, h.kappa, rnd_mode, p16=max_size <= 0xFFFF)
     dom = max(("argmax", "win", "kill"), key=lambda k: prof[k][0])
     assert all(isinstance(prof[k], tuple) for k in hm.KERNELS)
     peaks = measured_peaks()

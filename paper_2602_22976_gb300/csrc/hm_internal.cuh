@@ -15,12 +15,14 @@
 //                       counters are 16 bits wide, two to a word (edge e in
 //                       half e & 1 of word e >> 1): half the footprint, so
 //                       more of them stay in L2
+//   P0     uint32       the initial P words, copied by every match's init
 //   vrec   int4[n]      per-vertex record {T[v] as an edge j, cursor of T[v]
 //                       relative to the list start, list start, degree}
 //                       (Alg. 3's T plus V_id); T[v] = kCurMatched once v is
 //                       covered, kCurNone when v has no live edge. One 16-byte
 //                       load serves both the liveness check and the advance.
-//   firstj int32[n]     first entry of every vertex list (T[v] of round 1)
+//   firstj int32[n]     first entry of every vertex list (T[v] of round 1; round
+//                       1 writes T and the cursor of every record from it)
 //   list0/list1 int32[nregions*region] active vertex lists (ping-pong). The
 //                       list is cut into one region per warp of the argmax
 //                       grid; region g holds the active vertices of the
@@ -105,6 +107,7 @@ struct RoundArgs {
     const int32_t *order;
     uint8_t *alive;
     uint32_t *P;
+    const uint32_t *P0;    // initial P words (built once per handle)
     int4 *vrec;
     const int32_t *firstj;
     int32_t *list0;
@@ -158,6 +161,7 @@ struct Handle {
     float *weights = nullptr;   // input numbering, for the result weight
     uint8_t *alive = nullptr;
     uint32_t *P = nullptr;
+    uint32_t *P0 = nullptr;     // initial P words
     int4 *vrec = nullptr;
     int32_t *firstj = nullptr;
     int32_t *list0 = nullptr, *list1 = nullptr;

@@ -68,23 +68,14 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
     __syncthreads();
 }
 
+// Per-match reset: live flags, result mask, and the P counters from their
+// initial copy (P0). The vertex records' T and cursor are set by round 1.
 __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
-    const int64_t total = a.n > a.m ? a.n : a.m;
-    for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < total; i += (int64_t)gridDim.x * kT) {
-        if (i < a.m) {
-            a.alive[i] = 1;
-            a.inM[i] = 0;
-            if (a.graph) {  // every edge has two pins: no offsets to read
-                if ((i & 1) == 0) a.P[i >> 1] = i + 1 < a.m ? 0x00020002u : 2u;
-            } else if (!a.p16) {
-                a.P[i] = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
-            } else if ((i & 1) == 0) {  // the word of edges i and i + 1
-                const uint32_t lo = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
-                const uint32_t hi = i + 1 < a.m ? (uint32_t)(a.eoffj[i + 2] - a.eoffj[i + 1]) : 0u;
-                a.P[i >> 1] = lo | (hi << 16);
-            }
-        }
-        if (i < a.n) reinterpret_cast<int2 *>(a.vrec + i)[0] = make_int2(a.firstj[i], 0);
+    const int64_t pw = a.p16 ? (a.m + 1) / 2 : a.m;  // words of P
+    for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < a.m; i += (int64_t)gridDim.x * kT) {
+        a.alive[i] = 1;
+        a.inM[i] = 0;
+        if (i < pw) a.P[i] = __ldg(a.P0 + i);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevState *st = a.st;
@@ -100,6 +91,26 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
         st->lpack = st->live = st->kpack = 0;
+    }
+}
+
+// Initial P counters: |e| of every edge (two 16-bit halves a word when
+// p16), computed once per handle.
+__global__ void __launch_bounds__(kT) k_p0(RoundArgs a, uint32_t *__restrict__ p0) {
+    const int64_t pw = a.p16 ? (a.m + 1) / 2 : a.m;
+    for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < pw; i += (int64_t)gridDim.x * kT) {
+        uint32_t x;
+        if (a.graph) {  // every edge has two pins
+            x = 2 * i + 1 < a.m ? 0x00020002u : 2u;
+        } else if (!a.p16) {
+            x = (uint32_t)(a.eoffj[i + 1] - a.eoffj[i]);
+        } else {  // edges 2i and 2i + 1
+            const int64_t e = 2 * i;
+            const uint32_t lo = (uint32_t)(a.eoffj[e + 1] - a.eoffj[e]);
+            const uint32_t hi = e + 1 < a.m ? (uint32_t)(a.eoffj[e + 2] - a.eoffj[e + 1]) : 0u;
+            x = lo | (hi << 16);
+        }
+        p0[i] = x;
     }
 }
 
@@ -146,13 +157,19 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
     nb = -1;
     int64_t vb = 0, from = 0, end = 0, cn = 0;
     int32_t jj = 0;
-    if (ok) {
+    if (ok && r == 1) {
+        // every edge is live in round 1: T[v] is the first entry; the record
+        // (T, cursor) starts here
+        const int32_t f = __ldg(a.firstj + v);
+        reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(f, 0);
+        if (f >= 0) {
+            nb = f;
+            keep = true;
+        }
+    } else if (ok) {
         const int4 rec = a.vrec[v];
         if (rec.x >= 0) {
-            if (r == 1) {  // every edge is live in round 1: T[v] is the first entry
-                nb = rec.x;
-                keep = true;
-            } else if (__ldg(alive + rec.x)) {
+            if (__ldg(alive + rec.x)) {
                 keep = true;  // T[v] still live: unchanged
             } else {
                 vb = (int64_t)(uint32_t)rec.z;
@@ -620,7 +637,7 @@ void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent
 }
 
 unsigned init_grid(const Handle *h) {
-    return grid_for((uint64_t)std::max(h->n, h->m), kT, h->sm_count, 16);
+    return grid_for((uint64_t)std::max<int64_t>(h->m, 1), kT, h->sm_count, 16);
 }
 
 void capture_init(Handle *h, cudaStream_t s, void *ctx) {
@@ -743,6 +760,7 @@ RoundArgs round_args(const Handle *h) {
     a.order = h->order;
     a.alive = h->alive;
     a.P = h->P;
+    a.P0 = h->P0;
     a.vrec = h->vrec;
     a.firstj = h->firstj;
     a.list0 = h->list0;
@@ -775,6 +793,7 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     hm_status st;
     if ((st = dalloc(&h->alive, m, s, "alive")) != HM_OK) return st;
     if ((st = dalloc(&h->P, m, s, "P")) != HM_OK) return st;
+    if ((st = dalloc(&h->P0, h->p16 ? (m + 1) / 2 : m, s, "initial P")) != HM_OK) return st;
     if (!h->vrec) {  // normally built by hm_create
         set_error("vertex records missing");
         return HM_EINVAL;
@@ -791,6 +810,12 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     if ((st = dalloc(&h->items, h->item_cap, s, "kill items")) != HM_OK) return st;
     if ((st = dalloc(&h->inM, m, s, "result mask")) != HM_OK) return st;
     if ((st = apply_config(h, h->cfg)) != HM_OK) return st;
+    if (m) {
+        RoundArgs a = round_args(h);
+        k_p0<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(a, h->P0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "initial P");
+    }
     if ((st = dalloc(&h->stats, (uint64_t)kStatRounds * HM_STATS_COLS, s, "round stats")) != HM_OK) return st;
     if ((st = dalloc(&h->st, 1, s, "loop state")) != HM_OK) return st;
     if ((st = dalloc(&h->res_idx, m, s, "result ids")) != HM_OK) return st;
@@ -961,7 +986,7 @@ cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t 
 // the whole device, stalling every other stream (other handles, requests).
 void free_handle_buffers(Handle *h) {
     free_rand_buffers(h);
-    void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P,
+    void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P, h->P0,
                     h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win,
                     h->items, h->inM, h->stats, h->st, h->res_idx, h->res_w, h->res_part, h->res_bucket};
     cudaStream_t s = h->cap_stream;
