@@ -66,6 +66,47 @@ hm_status loop_status(const Handle *h) {
     }
 }
 
+void raise_pool_threshold(int dev);
+
+// Builds a handle from checked arguments (device inputs; see create_structures
+// for pins_ready).
+hm_status create_handle(hm_handle **out, int64_t n, int64_t m, uint64_t kappa, const int64_t *eoff,
+                        const int32_t *pins, const float *weights, uint64_t seed, bool weighted, cudaStream_t s,
+                        cudaEvent_t pins_ready) {
+    Handle *h = new (std::nothrow) Handle();
+    if (!h) return HM_ENOMEM;
+    h->n = n;
+    h->m = m;
+    h->kappa = kappa;
+    h->weighted = weighted;
+    h->seed = seed;
+    h->cap = m + 1;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    raise_pool_threshold(h->device);
+    hm_status st = HM_OK;
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        st = cuda_fail(e, "cudaStreamCreate");
+    if (st == HM_OK) st = create_structures(h, eoff, pins, weights, s, nullptr, 0, pins_ready);
+    if (st == HM_OK) st = alloc_round_state(h, s);
+    if (st == HM_OK) {
+        if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess)
+            st = cuda_fail(e, "cudaEventCreate");
+    }
+    if (st == HM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "hm_create");
+    if (st != HM_OK) {
+        cudaStreamSynchronize(s);
+        hm_destroy(reinterpret_cast<hm_handle *>(h));
+        return st;
+    }
+    *out = reinterpret_cast<hm_handle *>(h);
+    return HM_OK;
+}
+
 void raise_pool_threshold(int dev) {
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -130,38 +171,7 @@ hm_status hm_create(hm_handle **out, int64_t n, int64_t m, const int64_t *eoff, 
         if (!device_pointer(pins)) return einval("pins must be device memory");
     }
     if (m > 0 && n == 0) return einval("edges need vertices: n == 0 with m > 0");
-
-    Handle *h = new (std::nothrow) Handle();
-    if (!h) return HM_ENOMEM;
-    h->n = n;
-    h->m = m;
-    h->kappa = (uint64_t)ends[1];
-    h->weighted = weighted;
-    h->seed = seed;
-    h->cap = m + 1;
-    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) {
-        delete h;
-        return cuda_fail(e, "cudaGetDevice");
-    }
-    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-    raise_pool_threshold(h->device);
-    hm_status st = HM_OK;
-    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-        st = cuda_fail(e, "cudaStreamCreate");
-    if (st == HM_OK) st = create_structures(h, eoff, pins, weights, s);
-    if (st == HM_OK) st = alloc_round_state(h, s);
-    if (st == HM_OK) {
-        if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess)
-            st = cuda_fail(e, "cudaEventCreate");
-    }
-    if (st == HM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "hm_create");
-    if (st != HM_OK) {
-        cudaStreamSynchronize(s);
-        hm_destroy(reinterpret_cast<hm_handle *>(h));
-        return st;
-    }
-    *out = reinterpret_cast<hm_handle *>(h);
-    return HM_OK;
+    return create_handle(out, n, m, (uint64_t)ends[1], eoff, pins, weights, seed, weighted, s, nullptr);
 }
 
 hm_status hm_set_round_cap(hm_handle *hh, int64_t cap) {
@@ -376,29 +386,54 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
     if (eoff[0] != 0 || kappa < 0 || (uint64_t)kappa > 0xFFFFFFFFull)
         return einval("eoff[0] must be 0 and eoff[m] in [0, 2^32-1]");
     if (kappa > 0 && !pins) return einval("pins is NULL");
+    if (flags & ~(HM_UNWEIGHTED | HM_BORROW_INPUT | HM_VALIDATE)) return einval("unknown flag bits");
+    if (kappa < m) return einval("eoff[m] < m: some edge is empty or eoff decreases");
+    if (m > 0 && n == 0) return einval("edges need vertices: n == 0 with m > 0");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int dev = 0;
     cudaGetDevice(&dev);
     raise_pool_threshold(dev);
+    // The offsets and weights go first on the caller's stream: the edge phase
+    // of the build (their validation, the order, the edge offsets) needs only
+    // them and runs while the pins still cross the host link on a second
+    // stream; the pin phase waits for the pins' event.
     int64_t *d_eoff = nullptr;
     int32_t *d_pins = nullptr;
     float *d_w = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d_eoff, (size_t)(m + 1) * 8, s);
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_ew = nullptr, ev_pins = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ew, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_pins, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_eoff, (size_t)(m + 1) * 8, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_pins, (size_t)(kappa > 0 ? kappa : 1) * 4, s);
     if (e == cudaSuccess && weighted) e = cudaMallocAsync((void **)&d_w, (size_t)(m > 0 ? m : 1) * 4, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_eoff, eoff, (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && kappa > 0)
-        e = cudaMemcpyAsync(d_pins, pins, (size_t)kappa * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && weighted && m > 0)
         e = cudaMemcpyAsync(d_w, weights, (size_t)m * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_ew, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_ew, 0);
+    if (e == cudaSuccess && kappa > 0)
+        e = cudaMemcpyAsync(d_pins, pins, (size_t)kappa * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_pins, cs);
     hm_status st = HM_OK;
     if (e != cudaSuccess) st = cuda_fail(e, "hm_solve_host upload");
     hm_handle *h = nullptr;
-    if (st == HM_OK) st = hm_create(&h, n, m, d_eoff, d_pins, d_w, seed, flags, cuda_stream);
-    // inputs are no longer needed once hm_create returned
+    if (st == HM_OK)
+        st = create_handle(&h, n, m, (uint64_t)kappa, d_eoff, d_pins, d_w, seed, weighted, s, ev_pins);
+    // the inputs are no longer needed once the handle is built; s has waited
+    // for the pins' copy (or, on an early failure, waits for it here), and
+    // the host waits for it too: the caller may reuse its pins at once
+    if (ev_pins) {
+        cudaStreamWaitEvent(s, ev_pins, 0);
+        cudaEventSynchronize(ev_pins);
+    }
     if (d_eoff) cudaFreeAsync(d_eoff, s);
     if (d_pins) cudaFreeAsync(d_pins, s);
     if (d_w) cudaFreeAsync(d_w, s);
+    if (cs) cudaStreamDestroy(cs);
+    if (ev_ew) cudaEventDestroy(ev_ew);
+    if (ev_pins) cudaEventDestroy(ev_pins);
     if (st == HM_OK) st = hm_match(h, cuda_stream);
     if (st == HM_OK) st = hm_result(h, edges_out, count_out, rounds_out, weight_out);
     if (h) {

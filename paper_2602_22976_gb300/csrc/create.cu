@@ -288,7 +288,7 @@ struct Temps {
 
 hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
                             const float *weights, cudaStream_t s, const int64_t *inst_ebase,
-                            int32_t ninst) {
+                            int32_t ninst, cudaEvent_t pins_ready) {
     const int64_t n = h->n, m = h->m;
     const uint64_t kappa = h->kappa;
     struct Events {
@@ -316,8 +316,9 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     cudaError_t ce = cudaMemcpyAsync(derr, &init, sizeof init, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "error word upload");
 
-    // 1. validation
-    k_validate<<<gbig, kT, 0, s>>>(eoff, pins, h->weighted ? weights : nullptr, n, m, kappa, derr);
+    // 1. validation (the pins later, when they are still arriving)
+    k_validate<<<gbig, kT, 0, s>>>(eoff, pins_ready ? nullptr : pins, h->weighted ? weights : nullptr, n, m,
+                                   pins_ready ? 0 : kappa, derr);
     cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
     ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return cuda_fail(ce, "validation");
@@ -362,12 +363,9 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     if ((st = dalloc(&h->eoffj, (uint64_t)m + 1, s, "eoffj")) != HM_OK ||
         (st = dalloc(&h->pinsj, kappa, s, "pinsj")) != HM_OK)
         return st;
-    if (h->graph) {
-        // d = 2: offsets 2j, each edge's pair gathered in one 8-byte load;
-        // val receives j for both pin slots (pinsj and val: 8-byte aligned)
-        k_relabel_pairs<<<gm, kT, 0, s>>>(pins, order_u, m, h->eoffj, h->pinsj, val);
-    } else {
-        int64_t *szj = nullptr, *srcj = nullptr, *i64scratch = nullptr;
+    int64_t *srcj = nullptr;
+    if (!h->graph) {
+        int64_t *szj = nullptr, *i64scratch = nullptr;
         if ((st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
             (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
             (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
@@ -377,18 +375,36 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
         if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
         tmp.drop(szj);
         tmp.drop(i64scratch);
-        // val now receives j for every pin slot; the relabelled pins double as
-        // the keys of the vertex sort
-        {
-            const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;
-            int32_t *first = nullptr;
-            if ((st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK) return st;
-            k_tile_first<<<gm, kT, 0, s>>>(h->eoffj, m, ntiles, first);
-            if (ntiles > 0)
-                k_relabel<<<(unsigned)ntiles, kT, 0, s>>>(pins, srcj, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
-            tmp.drop(first);
-            tmp.drop(srcj);
+    }
+    if (pins_ready) {
+        // the pins have arrived: validate them before anything is indexed by them
+        cudaStreamWaitEvent(s, pins_ready, 0);
+        if (kappa) k_validate<<<gbig, kT, 0, s>>>(eoff, pins, nullptr, n, 0, kappa, derr);
+        cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
+        ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "pin validation");
+        if (herr.flags & kErrPin) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "pin at position %llu is outside [0, n)", herr.first[1]);
+            set_error(buf);
+            return HM_EINVAL;
         }
+    }
+    if (h->graph) {
+        // d = 2: offsets 2j, each edge's pair gathered in one 8-byte load;
+        // val receives j for both pin slots (pinsj and val: 8-byte aligned)
+        k_relabel_pairs<<<gm, kT, 0, s>>>(pins, order_u, m, h->eoffj, h->pinsj, val);
+    } else {
+        // val receives j for every pin slot; the relabelled pins double as
+        // the keys of the vertex sort
+        const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;
+        int32_t *first = nullptr;
+        if ((st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK) return st;
+        k_tile_first<<<gm, kT, 0, s>>>(h->eoffj, m, ntiles, first);
+        if (ntiles > 0)
+            k_relabel<<<(unsigned)ntiles, kT, 0, s>>>(pins, srcj, h->eoffj, first, m, kappa, ntiles, h->pinsj, val);
+        tmp.drop(first);
+        tmp.drop(srcj);
     }
     cudaEventRecord(ev.e[3], s);
 

@@ -246,9 +246,13 @@ cudaError_t compact_flags(const uint8_t *flags, uint64_t n, const float *w, int3
 // ---- create (create.cu) ----
 // inst_ebase (device, ninst entries): first edge of each instance when the
 // input is a union of independent instances (local hash priorities), else null.
+// pins_ready (or null): the pins are still being copied and this event
+// marks their arrival; the edge phase (validation of offsets and weights,
+// the order, the edge offsets) runs first, then s waits for the event and
+// the pins are validated before they are used.
 hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
                             const float *weights, cudaStream_t s, const int64_t *inst_ebase = nullptr,
-                            int32_t ninst = 0);
+                            int32_t ninst = 0, cudaEvent_t pins_ready = nullptr);
 
 // ---- rounds (rounds.cu) ----
 RoundArgs round_args(const Handle *h);

@@ -190,6 +190,24 @@ def test_solve_host_matches_handle_path():
     assert np.array_equal(ru.edges, ou.edges) and ru.rounds == ou.rounds
 
 
+def test_solve_host_rejects_bad_input():
+    """hm_solve_host uploads the pins while the edge phase of the build runs:
+    a bad weight fails before the pins are used, a bad pin fails when they
+    arrive; both report HM_EINVAL, and the next call works."""
+    h = synth.large(seed=6, n=50_000, m=100_000)
+    bad_w = synth.Hypergraph(h.n, h.m, h.eoff, h.pins, h.weights.copy(), h.seed)
+    bad_w.weights[123] = -1.0
+    r = hmlib.solve_host(bad_w, allow=(OK, EINVAL))
+    assert r.status == EINVAL and "weight" in hmlib.last_error()
+    bad_p = synth.Hypergraph(h.n, h.m, h.eoff, h.pins.copy(), h.weights, h.seed)
+    bad_p.pins[h.kappa // 2] = h.n
+    r = hmlib.solve_host(bad_p, allow=(OK, EINVAL))
+    assert r.status == EINVAL and "pin" in hmlib.last_error()
+    o = oracle.match(h)
+    r = hmlib.solve_host(h)
+    assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+
+
 def test_random_access_probe():
     r = hmlib.probe_random_access(1 << 20, 2_000_000)
     assert set(r) == set(hmlib.PROBES) and all(v > 0 for v in r.values())
