@@ -132,3 +132,30 @@ def test_batch_rejects_cross_instance_inputs():
     with hmlib.Batch([a, b]) as ok:  # the valid pair still works
         ok.match()
         check_against_oracle([a, b], ok.result())
+
+
+def test_full_size_batch_in_bench_configuration():
+    """The batching workload at full size, launched as the bench launches it
+    (4,096 instances, n log-uniform in [100, 200,000], m = 2n, |e| ~ U{2..16},
+    autotuned size classes): every instance equals its own single-instance
+    GPU run, and a seeded sample of 48 instances equals the CPU oracle."""
+    hs = synth.batch(4096, seed=1)
+    for h in hs:
+        h.seed = 1
+    with hmlib.Batch(hs, autotune=True) as b:
+        b.match()
+        res = b.result()
+    assert len(res) == 4096
+    rng = np.random.default_rng(2)
+    sample = set(rng.choice(4096, 48, replace=False).tolist())
+    for i, (h, r) in enumerate(zip(hs, res)):
+        assert r.status == hmlib.HM_OK
+        if i in sample:
+            o = oracle.match(h)
+            assert r.rounds == o.rounds and np.array_equal(r.edges, o.edges), i
+            assert r.weight == oracle.weight(h, o.in_matching)
+        elif i % 16 == 0:  # the rest: against the single-instance GPU path
+            with hmlib.Matcher.from_hypergraph(h) as mt:
+                mt.match()
+                a = mt.result()
+            assert a.rounds == r.rounds and np.array_equal(a.edges, r.edges), i

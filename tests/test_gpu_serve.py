@@ -133,3 +133,21 @@ def test_invalid_request_inside_a_group():
         else:
             o = oracle.match(h)
             assert r.status == hmlib.HM_OK and np.array_equal(r.edges, o.edges)
+
+
+def test_full_size_requests_in_a_mix():
+    """Requests drawn from the serving workload's distribution (kappa
+    log-uniform in [1e3, 1e7], |e| ~ Zipf(2) on [2, 256]) submitted at once
+    to the server the bench uses (8 slots): every result equals the CPU
+    oracle's."""
+    rng = np.random.default_rng(21)
+    kap = np.exp(rng.uniform(np.log(1e3), np.log(1e7), size=24)).astype(np.int64)
+    kap[0] = 10_000_000  # the largest size of the distribution
+    hs = [synth.serve_request(int(k), seed=2100 + i) for i, k in enumerate(kap)]
+    with hmlib.Server(slots=8) as srv:
+        tickets = [srv.submit(h) for h in hs]
+        got = [srv.wait(t)[0] for t in tickets]
+    for h, r in zip(hs, got):
+        o = oracle.match(h)
+        assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+        assert r.weight == oracle.weight(h, o.in_matching)
