@@ -69,10 +69,10 @@ hm_status loop_status(const Handle *h) {
 void raise_pool_threshold(int dev);
 
 // Builds a handle from checked arguments (device inputs; see create_structures
-// for pins_ready).
+// for feed).
 hm_status create_handle(hm_handle **out, int64_t n, int64_t m, uint64_t kappa, const int64_t *eoff,
                         const int32_t *pins, const float *weights, uint64_t seed, bool weighted, cudaStream_t s,
-                        cudaEvent_t pins_ready) {
+                        const PinChunks *feed) {
     Handle *h = new (std::nothrow) Handle();
     if (!h) return HM_ENOMEM;
     h->n = n;
@@ -91,7 +91,7 @@ hm_status create_handle(hm_handle **out, int64_t n, int64_t m, uint64_t kappa, c
     hm_status st = HM_OK;
     if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         st = cuda_fail(e, "cudaStreamCreate");
-    if (st == HM_OK) st = create_structures(h, eoff, pins, weights, s, nullptr, 0, pins_ready);
+    if (st == HM_OK) st = create_structures(h, eoff, pins, weights, s, nullptr, 0, feed);
     if (st == HM_OK) st = alloc_round_state(h, s);
     if (st == HM_OK) {
         if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess)
@@ -395,16 +395,23 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
     raise_pool_threshold(dev);
     // The offsets and weights go first on the caller's stream: the edge phase
     // of the build (their validation, the order, the edge offsets) needs only
-    // them and runs while the pins still cross the host link on a second
-    // stream; the pin phase waits for the pins' event.
+    // them and runs while the pins still cross the host link, in chunks, on a
+    // second stream; each chunk is relabelled as soon as it has arrived.
+    constexpr int kChunks = 8;
     int64_t *d_eoff = nullptr;
     int32_t *d_pins = nullptr;
     float *d_w = nullptr;
     cudaStream_t cs = nullptr;
-    cudaEvent_t ev_ew = nullptr, ev_pins = nullptr;
+    cudaEvent_t ev_ew = nullptr, ev_pins[kChunks] = {};
+    uint64_t begin[kChunks + 1];
+    for (int c = 0; c <= kChunks; ++c) {  // chunk starts on relabel-tile boundaries
+        const uint64_t x = (uint64_t)kappa * (uint64_t)c / kChunks;
+        begin[c] = c == kChunks ? (uint64_t)kappa : x / kRelabelTile * kRelabelTile;
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ew, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_pins, cudaEventDisableTiming);
+    for (int c = 0; c < kChunks && e == cudaSuccess; ++c)
+        e = cudaEventCreateWithFlags(&ev_pins[c], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_eoff, (size_t)(m + 1) * 8, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_pins, (size_t)(kappa > 0 ? kappa : 1) * 4, s);
     if (e == cudaSuccess && weighted) e = cudaMallocAsync((void **)&d_w, (size_t)(m > 0 ? m : 1) * 4, s);
@@ -413,27 +420,30 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
         e = cudaMemcpyAsync(d_w, weights, (size_t)m * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_ew, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_ew, 0);
-    if (e == cudaSuccess && kappa > 0)
-        e = cudaMemcpyAsync(d_pins, pins, (size_t)kappa * 4, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaEventRecord(ev_pins, cs);
+    for (int c = 0; c < kChunks && e == cudaSuccess; ++c) {
+        if (begin[c + 1] > begin[c])
+            e = cudaMemcpyAsync(d_pins + begin[c], pins + begin[c], (size_t)(begin[c + 1] - begin[c]) * 4,
+                                cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_pins[c], cs);
+    }
     hm_status st = HM_OK;
     if (e != cudaSuccess) st = cuda_fail(e, "hm_solve_host upload");
     hm_handle *h = nullptr;
-    if (st == HM_OK)
-        st = create_handle(&h, n, m, (uint64_t)kappa, d_eoff, d_pins, d_w, seed, weighted, s, ev_pins);
-    // the inputs are no longer needed once the handle is built; s has waited
-    // for the pins' copy (or, on an early failure, waits for it here), and
-    // the host waits for it too: the caller may reuse its pins at once
-    if (ev_pins) {
-        cudaStreamWaitEvent(s, ev_pins, 0);
-        cudaEventSynchronize(ev_pins);
+    if (st == HM_OK) {
+        const PinChunks feed{kChunks, begin, ev_pins};
+        st = create_handle(&h, n, m, (uint64_t)kappa, d_eoff, d_pins, d_w, seed, weighted, s, &feed);
     }
+    // the inputs are no longer needed once the handle is built; every copy
+    // issued on the copy stream has finished before they are freed (on an
+    // early failure too), and the caller may reuse its pins at once
+    if (cs) cudaStreamSynchronize(cs);
     if (d_eoff) cudaFreeAsync(d_eoff, s);
     if (d_pins) cudaFreeAsync(d_pins, s);
     if (d_w) cudaFreeAsync(d_w, s);
     if (cs) cudaStreamDestroy(cs);
     if (ev_ew) cudaEventDestroy(ev_ew);
-    if (ev_pins) cudaEventDestroy(ev_pins);
+    for (auto &x : ev_pins)
+        if (x) cudaEventDestroy(x);
     if (st == HM_OK) st = hm_match(h, cuda_stream);
     if (st == HM_OK) st = hm_result(h, edges_out, count_out, rounds_out, weight_out);
     if (h) {

@@ -135,7 +135,7 @@ __global__ void k_sizes_j(const int64_t *__restrict__ eoff, const uint32_t *__re
 // the input (srcj), locates each slot's edge by binary search in shared
 // memory, and writes both outputs coalesced whatever the edge sizes. One
 // tile per block: the GPU keeps many tiles' dependent loads in flight.
-constexpr int kRelTile = 2048;
+constexpr int kRelTile = kRelabelTile;
 
 // first[t] = the edge that contains output slot t*kRelTile.
 __global__ void k_tile_first(const int64_t *__restrict__ eoffj, int64_t m, uint64_t ntiles,
@@ -176,6 +176,60 @@ __global__ void __launch_bounds__(kT) k_relabel(const int32_t *__restrict__ pins
         pinsj[p] = pins[s_src[lo] + (int64_t)(p - (uint64_t)s_off[lo])];
         jval[p] = (uint32_t)(j0 + lo);
     }
+}
+
+// Input-driven relabel of the pin tiles [t0, t1) (tiles of kRelTile
+// consecutive INPUT pins, first[t] = the input edge holding the tile's
+// first pin): a block loads the input offsets of the tile's edges and, per
+// edge, its relabelled id j and the first slot of its pins in j order, then
+// writes every pin to its slot. A block reads only its own tile, so the
+// tiles can run as soon as their pins have arrived. Pins outside [0, n) are
+// reported (and written; the build stops before anything indexes by them).
+__global__ void __launch_bounds__(kT) k_relabel_in(const int32_t *__restrict__ pins, const int64_t *__restrict__ eoff,
+                                                  const int32_t *__restrict__ jof,
+                                                  const int64_t *__restrict__ eoffj,
+                                                  const int32_t *__restrict__ first, int64_t m, int64_t n,
+                                                  uint64_t kappa, uint64_t ntiles, uint64_t t0,
+                                                  int32_t *__restrict__ pinsj, uint32_t *__restrict__ jval,
+                                                  CreateErr *err) {
+    __shared__ int64_t s_off[kRelTile + 1];  // input offsets of the tile's edges
+    __shared__ int64_t s_dst[kRelTile];      // their first slot in j order
+    __shared__ int32_t s_j[kRelTile];        // their relabelled ids
+    const uint64_t t = t0 + blockIdx.x;
+    if (t >= ntiles) return;
+    const uint64_t p0 = t * kRelTile;
+    const uint64_t p1 = p0 + kRelTile < kappa ? p0 + kRelTile : kappa;
+    const int64_t e0 = first[t];
+    const int64_t e1 = t + 1 < ntiles ? first[t + 1] : m - 1;  // last edge touching the tile
+    const int ne = (int)(e1 - e0 + 1);                          // <= kRelTile + 1
+    for (int k = threadIdx.x; k <= ne && k <= kRelTile; k += kT) {
+        s_off[k] = eoff[e0 + k];
+        if (k < ne && k < kRelTile) {
+            const int32_t j = __ldg(jof + e0 + k);
+            s_j[k] = j;
+            s_dst[k] = __ldg(eoffj + j);
+        }
+    }
+    __syncthreads();
+    const int hi0 = (ne < kRelTile ? ne : kRelTile) - 1;
+    for (uint64_t p = p0 + threadIdx.x; p < p1; p += kT) {
+        int lo = 0, hi = hi0;  // last k with s_off[k] <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((uint64_t)s_off[mid] <= p) lo = mid; else hi = mid - 1;
+        }
+        const int32_t v = pins[p];
+        if (v < 0 || (int64_t)v >= n) report(err, kErrPin, 1, p);
+        const int64_t slot = s_dst[lo] + (int64_t)(p - (uint64_t)s_off[lo]);
+        pinsj[slot] = v;
+        jval[slot] = (uint32_t)s_j[lo];
+    }
+}
+
+// jof[order[j]] = j: the relabelled id of every input edge.
+__global__ void k_inverse(const uint32_t *__restrict__ order, int64_t m, int32_t *__restrict__ jof) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        jof[order[j]] = (int32_t)j;
 }
 
 // d = 2: edge j's pins are the pair of input edge order[j]; eoffj[j] = 2j.
@@ -288,7 +342,7 @@ struct Temps {
 
 hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
                             const float *weights, cudaStream_t s, const int64_t *inst_ebase,
-                            int32_t ninst, cudaEvent_t pins_ready) {
+                            int32_t ninst, const PinChunks *feed) {
     const int64_t n = h->n, m = h->m;
     const uint64_t kappa = h->kappa;
     struct Events {
@@ -317,8 +371,8 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     if (ce != cudaSuccess) return cuda_fail(ce, "error word upload");
 
     // 1. validation (the pins later, when they are still arriving)
-    k_validate<<<gbig, kT, 0, s>>>(eoff, pins_ready ? nullptr : pins, h->weighted ? weights : nullptr, n, m,
-                                   pins_ready ? 0 : kappa, derr);
+    k_validate<<<gbig, kT, 0, s>>>(eoff, feed ? nullptr : pins, h->weighted ? weights : nullptr, n, m,
+                                   feed ? 0 : kappa, derr);
     cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
     ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return cuda_fail(ce, "validation");
@@ -363,22 +417,11 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
     if ((st = dalloc(&h->eoffj, (uint64_t)m + 1, s, "eoffj")) != HM_OK ||
         (st = dalloc(&h->pinsj, kappa, s, "pinsj")) != HM_OK)
         return st;
-    int64_t *srcj = nullptr;
-    if (!h->graph) {
-        int64_t *szj = nullptr, *i64scratch = nullptr;
-        if ((st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
-            (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
-            (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
-            return st;
-        k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj, srcj);
-        ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
-        if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
-        tmp.drop(szj);
-        tmp.drop(i64scratch);
-    }
-    if (pins_ready) {
-        // the pins have arrived: validate them before anything is indexed by them
-        cudaStreamWaitEvent(s, pins_ready, 0);
+    if (feed && h->graph) {
+        // d = 2: an edge holds only two pins, so relabelling as the chunks
+        // arrive would cost two random reads per pair; gather the pairs once
+        // every chunk is in, after checking the pins
+        for (int c = 0; c < feed->chunks; ++c) cudaStreamWaitEvent(s, feed->ev[c], 0);
         if (kappa) k_validate<<<gbig, kT, 0, s>>>(eoff, pins, nullptr, n, 0, kappa, derr);
         cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
         ce = cudaStreamSynchronize(s);
@@ -389,12 +432,65 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
             set_error(buf);
             return HM_EINVAL;
         }
-    }
-    if (h->graph) {
+        k_relabel_pairs<<<gm, kT, 0, s>>>(pins, order_u, m, h->eoffj, h->pinsj, val);
+    } else if (feed) {
+        // edge offsets in j order, the inverse order, the input tiles' first
+        // edges; then every chunk of pins is relabelled once it has arrived
+        {
+            int64_t *szj = nullptr, *srcj = nullptr, *i64scratch = nullptr;
+            if ((st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
+                (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
+                (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
+                return st;
+            k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj, srcj);
+            ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
+            tmp.drop(szj);
+            tmp.drop(srcj);
+            tmp.drop(i64scratch);
+        }
+        const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;
+        int32_t *jof = nullptr, *first = nullptr;
+        if ((st = tmp.get(&jof, (uint64_t)m, "inverse order")) != HM_OK ||
+            (st = tmp.get(&first, ntiles, "relabel tiles")) != HM_OK)
+            return st;
+        k_inverse<<<gm, kT, 0, s>>>(order_u, m, jof);
+        k_tile_first<<<gm, kT, 0, s>>>(eoff, m, ntiles, first);
+        for (int c = 0; c < feed->chunks; ++c) {
+            cudaStreamWaitEvent(s, feed->ev[c], 0);
+            const uint64_t ta = feed->begin[c] / kRelTile;
+            const uint64_t tb = (feed->begin[c + 1] + kRelTile - 1) / kRelTile;
+            if (tb > ta)
+                k_relabel_in<<<(unsigned)(tb - ta), kT, 0, s>>>(pins, eoff, jof, h->eoffj, first, m, n, kappa,
+                                                                 ntiles, ta, h->pinsj, val, derr);
+        }
+        tmp.drop(jof);
+        tmp.drop(first);
+        // the pins must be valid before the vertex CSR indexes by them
+        cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
+        ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "relabel");
+        if (herr.flags & kErrPin) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "pin at position %llu is outside [0, n)", herr.first[1]);
+            set_error(buf);
+            return HM_EINVAL;
+        }
+    } else if (h->graph) {
         // d = 2: offsets 2j, each edge's pair gathered in one 8-byte load;
         // val receives j for both pin slots (pinsj and val: 8-byte aligned)
         k_relabel_pairs<<<gm, kT, 0, s>>>(pins, order_u, m, h->eoffj, h->pinsj, val);
     } else {
+        int64_t *szj = nullptr, *srcj = nullptr, *i64scratch = nullptr;
+        if ((st = tmp.get(&szj, (uint64_t)m, "edge sizes")) != HM_OK ||
+            (st = tmp.get(&srcj, (uint64_t)m, "edge sources")) != HM_OK ||
+            (st = tmp.get(&i64scratch, scan_scratch_elems((uint64_t)m), "scan scratch")) != HM_OK)
+            return st;
+        k_sizes_j<<<gm, kT, 0, s>>>(eoff, order_u, m, szj, srcj);
+        ce = exclusive_scan_i64(szj, h->eoffj, (uint64_t)m, h->eoffj + m, i64scratch, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "edge offsets");
+        tmp.drop(szj);
+        tmp.drop(i64scratch);
         // val receives j for every pin slot; the relabelled pins double as
         // the keys of the vertex sort
         const uint64_t ntiles = (kappa + kRelTile - 1) / kRelTile;

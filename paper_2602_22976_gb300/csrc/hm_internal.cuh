@@ -246,13 +246,23 @@ cudaError_t compact_flags(const uint8_t *flags, uint64_t n, const float *w, int3
 // ---- create (create.cu) ----
 // inst_ebase (device, ninst entries): first edge of each instance when the
 // input is a union of independent instances (local hash priorities), else null.
-// pins_ready (or null): the pins are still being copied and this event
-// marks their arrival; the edge phase (validation of offsets and weights,
-// the order, the edge offsets) runs first, then s waits for the event and
-// the pins are validated before they are used.
+// Pins still crossing the host link, in chunks of consecutive pins: chunk c
+// covers pins [begin[c], begin[c+1]) (begin[0] = 0, begin[chunks] = kappa,
+// every other begin a multiple of kRelabelTile) and event ev[c] marks its
+// arrival on the device.
+constexpr int kRelabelTile = 2048;
+struct PinChunks {
+    int chunks;
+    const uint64_t *begin;   // host, chunks + 1 entries
+    const cudaEvent_t *ev;   // host, chunks entries
+};
+// feed (or null): the edge phase (validation of offsets and weights, the
+// order, the edge offsets) runs first; then each chunk of pins is relabelled
+// as soon as it has arrived, the pins are validated on the way, and their
+// validity is checked before the vertex CSR is built from them.
 hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
                             const float *weights, cudaStream_t s, const int64_t *inst_ebase = nullptr,
-                            int32_t ninst = 0, cudaEvent_t pins_ready = nullptr);
+                            int32_t ninst = 0, const PinChunks *feed = nullptr);
 
 // ---- rounds (rounds.cu) ----
 RoundArgs round_args(const Handle *h);
