@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="batch workload: skip the one-hm_match-per-instance comparison")
+    ap.add_argument("--one-class", action="store_true",
+                    help="batch workload: every instance in one union (HM_ONE_CLASS) instead of size classes")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide n and m of the workload (smaller cases for profiler captures)")
     ap.add_argument("--noise", type=float, default=0.0,
@@ -311,7 +313,7 @@ def run_batch(args, world, rank, local):
         h.seed = args.seed
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    b = hm.Batch(hs, autotune=True)
+    b = hm.Batch(hs, autotune=True, one_class=args.one_class)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -366,7 +368,8 @@ def run_batch(args, world, rank, local):
         "config": {"workload": WORKLOADS["batch"]["desc"] + (f" ({count} instances)" if count != 4096 else ""),
                    "instances": count, "sum_kappa": int(sum(h.kappa for h in hs)),
                    "sum_n": int(sum(h.n for h in hs)), "size_classes": int(ncls),
-                   "class_launch_configs": cfg.tolist(), "l2": "inputs larger than L2"},
+                   "class_launch_configs": cfg.tolist(), "l2": "inputs larger than L2",
+                   "classes": "one union (HM_ONE_CLASS)" if args.one_class else "size classes by kappa (factors of 4)"},
         "instances_per_s": count * world * args.steps / (t_max / 1e3),
         "time_to_matching_ms": {"median": statistics.median(step_ms)},
         "create_s": t_create, "generate_s": t_gen,
