@@ -597,6 +597,7 @@ def run_ours(args, world, rank, local):
             e2e = {"value": h.kappa * res.rounds / te, "unit": "pins/s", "ms_per_step": te * 1e3,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 8 + 64)}
         cpu = None
+        cpu_greedy = None
         parity = None
         if not args.no_cpu_baseline:
             import oracle
@@ -608,6 +609,18 @@ def run_ours(args, world, rank, local):
             cpu = {"value": h.kappa * o.rounds / tc, "unit": "pins/s", "cores": cpu_cores_used(),
                    "kind": "oracle", "sample": f"the full instance, one oracle run ({tc:.1f} s)",
                    "active_pins": int(o.round_stats[:, 1].sum())}
+            if not rnd_mode:
+                # the paper's single-core Greedy baseline: sort by priority, take an
+                # edge when all its pins are free (same order, so the same matching)
+                t0 = time.perf_counter()
+                g = oracle.greedy(h)
+                tg = time.perf_counter() - t0
+                gpu_ms = t_max / args.steps
+                cpu_greedy = {"ms": tg * 1e3, "cores": 1, "kind": "sequential greedy (oracle)",
+                              "same_matching": bool(np.array_equal(np.flatnonzero(g), res.edges)),
+                              "speedup_of_match": tg * 1e3 / gpu_ms}
+                if e2e:
+                    cpu_greedy["speedup_end_to_end"] = tg * 1e3 / e2e["ms_per_step"]
         out = {
             "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -637,6 +650,7 @@ def run_ours(args, world, rank, local):
             "round_ms_argmax_win_kill": round_ms,
             "round_stats": stats.tolist(),
             "cpu_baseline": cpu,
+            "cpu_greedy": cpu_greedy,
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": launches * args.steps,

@@ -376,6 +376,9 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
         }
         if (lane == 0) cnt_out[g] = kept;
     }
+    // a block with nothing to report (most blocks in the late rounds) skips
+    // the block-level combining below
+    if (!__syncthreads_or(kept != 0 || won != 0 || adv != 0 || props != 0)) return;
     if (lane == 0) {
         s_keep[wib] = kept;
         s_won[wib] = won;
@@ -413,6 +416,7 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    if ((uint64_t)blockIdx.x * kT >= nw) return;  // no winner for any warp of this block (uniform)
     unsigned long long winpins = 0;
     for (uint64_t w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
         const int32_t j = w0 + lane < nw ? a.win[w0 + lane] : -1;
