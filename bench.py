@@ -204,6 +204,35 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
     return b
 
 
+def random_access_roofline(stats: np.ndarray, prof: dict, ra: dict, random: bool) -> dict | None:
+    """The round kernels are bound by random single-element accesses, not by
+    bytes: a lower bound on each kernel's time is its random accesses at this
+    GPU's measured rates (hm_probe_random_access: 1-byte loads, 1-byte
+    stores, returning 4-byte atomics). frac = that bound / the kernel's time.
+    Counted from hm_round_stats, fixed order only: k_argmax does one live-flag
+    load per active vertex and per skipped entry from round 2 on and one
+    returning atomic per proposal; k_kill stores every target in round 1 and
+    loads every target's flag from round 2 on (the stores to the live ones
+    are left out, so its bound is low)."""
+    if random:
+        return None
+    ACT, ADV, PROP = 0, 1, 2
+    KILL = 5
+    s = stats.astype(np.float64)
+    loads = float(s[1:, ACT].sum() + s[1:, ADV].sum())
+    atoms = float(s[:, PROP].sum())
+    k_loads = float(s[1:, KILL].sum())
+    k_stores = float(s[:1, KILL].sum())
+    out = {}
+    for name, t_ms, bound in (
+            ("argmax", prof["argmax"][0], loads / (ra["load1B"] * 1e9) + atoms / (ra["atomic4B"] * 1e9)),
+            ("kill", prof["kill"][0], k_loads / (ra["load1B"] * 1e9) + k_stores / (ra["store1B"] * 1e9))):
+        out[name] = {"bound_ms": bound * 1e3, "ms": t_ms, "frac": bound * 1e3 / t_ms if t_ms > 0 else None}
+    out["note"] = ("time of each kernel's random flag loads, stores and atomics at the measured random-access "
+                   "rates, over its measured time")
+    return out
+
+
 # kernel step of the bench line -> (row name in profiles/traffic.md, its source file)
 TRAFFIC_ROWS = {
     ("argmax", False): ("k_argmax", "rounds.cu"),
@@ -537,6 +566,7 @@ def run_ours(args, world, rank, local):
     # random-access ceilings of this GPU for an array the size of the live flags
     ra = hm.probe_random_access(max(h.m, 1 << 20), 200_000_000)
     kills = float(stats[:, hm.STAT_COLUMNS.index("kills")].sum())
+    rar = random_access_roofline(stats, prof, ra, rnd_mode)
     loop_ms = sum(prof[k][0] for k in hm.KERNELS)
     rounds_run = int(prof["argmax"][1])
     # init + three kernels per round (argmax, win, kill with the round end);
@@ -646,6 +676,7 @@ def run_ours(args, world, rank, local):
                 "kill_entries_gops": kills / (prof["kill"][0] / 1e3) / 1e9,
                 "note": "kill reads each target flag (rounds >= 2) and writes the live ones; "
                         "its bound is the random 1-byte load/store rate, not HBM bandwidth"},
+            "random_access_roofline": rar,
             "kernels": per_kernel,
             "round_ms_argmax_win_kill": round_ms,
             "round_stats": stats.tolist(),
