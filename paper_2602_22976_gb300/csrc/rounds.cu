@@ -498,8 +498,11 @@ __device__ void round_end(const RoundArgs &a) {
 // From round 2 on most targets are already dead (they sit behind the
 // cursors of other vertices), and on this GPU a random 1-byte load costs
 // less than half of a random 1-byte store, so the flag is read first and
-// only live targets are written. In round 1 every target is live: plain
-// stores. The block that finishes last (a ticket counter; every other
+// only live targets are cleared (in round 1 every target is live). A flag
+// is cleared by an atomic AND on its 32-bit word with the other three bytes
+// kept: a random reduction without a returned value runs at about 1.5x the
+// rate of a random 1-byte store here (the flag array is allocated in whole
+// words). The block that finishes last (a ticket counter; every other
 // block has read the round's state by then) runs round_end.
 template <int S>  // the edge id of list entry p is vadj[p * S]
 __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
@@ -569,7 +572,9 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
                     for (int u = 0; u < 4; ++u) wr[u] = jj[u] >= 0 && (!check || __ldcg(alive + jj[u]) != 0);
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        if (wr[u]) alive[jj[u]] = 0;
+                        if (wr[u])  // clear the flag byte with a reduction on its word
+                            atomicAnd(reinterpret_cast<unsigned int *>(alive) + (jj[u] >> 2),
+                                      ~(0xFFu << (8 * (jj[u] & 3))));
                 }
                 q = stop;
                 i += 32;
@@ -795,7 +800,7 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
     h->win_cap = std::min(n, m) + 1;
     h->item_cap = n + 1;  // one kill range per newly matched vertex
     hm_status st;
-    if ((st = dalloc(&h->alive, m, s, "alive")) != HM_OK) return st;
+    if ((st = dalloc(&h->alive, (m + 3) / 4 * 4, s, "alive")) != HM_OK) return st;  // whole words
     if ((st = dalloc(&h->P, m, s, "P")) != HM_OK) return st;
     if ((st = dalloc(&h->P0, h->p16 ? (m + 1) / 2 : m, s, "initial P")) != HM_OK) return st;
     if (!h->vrec) {  // normally built by hm_create
