@@ -159,3 +159,15 @@ def test_full_size_batch_in_bench_configuration():
                 mt.match()
                 a = mt.result()
             assert a.rounds == r.rounds and np.array_equal(a.edges, r.edges), i
+
+
+def test_batch_of_graphs():
+    """A batch whose instances are all graphs: each size class's union is a
+    graph and takes the pair paths of the build and the loop."""
+    hs = [synth.rgg(seed=40 + i, n=int(n), avg_degree=d) for i, (n, d) in
+          enumerate([(500, 6.0), (3000, 16.0), (20000, 10.0), (800, 30.0), (60000, 16.0)])]
+    for h in hs:
+        h.seed = 1
+    with hmlib.Batch(hs) as b:
+        b.match()
+        check_against_oracle(hs, b.result())

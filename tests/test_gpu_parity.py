@@ -190,6 +190,17 @@ def test_solve_host_matches_handle_path():
     assert np.array_equal(ru.edges, ou.edges) and ru.rounds == ou.rounds
 
 
+def test_solve_host_graph_and_chunks():
+    """hm_solve_host on a graph (pairs gathered once every chunk of pins is
+    in) and on inputs smaller than one chunk of the upload."""
+    for h in (synth.rgg(seed=8, n=60_000), synth.small(seed=9, n=300, m=500),
+              synth.from_edges(3, [[0, 1]], [0.5], seed=1)):
+        o = oracle.match(h)
+        r = hmlib.solve_host(h)
+        assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+        assert r.weight == oracle.weight(h, o.in_matching)
+
+
 def test_solve_host_rejects_bad_input():
     """hm_solve_host uploads the pins while the edge phase of the build runs:
     a bad weight fails before the pins are used, a bad pin fails when they

@@ -167,3 +167,10 @@ def test_invalid_amplitude():
 def test_full_size_powerlaw_random():
     """n=10M, m=20M power-law hypergraph (kappa ~ 2.02e8), re-randomised rounds."""
     assert_parity(synth.large(), 1.0)
+
+
+def test_graph_rgg_random():
+    """Re-randomised rounds on a graph (every edge has two pins: the proposal
+    takes |e| = 2 without reading offsets)."""
+    h = synth.rgg(seed=4, n=40_000, avg_degree=12.0)
+    assert_parity(h, 1.0)
