@@ -3,7 +3,7 @@
 hypergraph: n=10M vertices, m=20M edges, |e| ~ Zipf(2) on [2,1024], vertex
 degrees power-law (gamma=2.2), float32 weights in (0,1], kappa ~ 2.02e8.
 
-One step = one hm_match (the whole round loop, all four kernels of every
+One step = one hm_match (the whole round loop, all three kernels of every
 round, as one CUDA graph) on inputs already resident in HBM.
 
   value        kappa * rounds * steps / device time      (pins/s, whole job)

@@ -164,7 +164,7 @@ hm_status hm_launch_config(hm_handle *h, const int32_t *set, int32_t *get);
 
 /*
  * hm_autotune - pick the launch shape of this handle by measurement: a
- * coordinate-descent search over the kill item size and the blocks per SM
+ * coordinate-descent search over the least kill slice per warp and the blocks per SM
  * of the three round kernels, each candidate timed as the median of three
  * hm_match graph launches (CUDA events on `cuda_stream`). Leaves the best
  * config applied and reports it (HOST int32[4], as hm_launch_config) and its
