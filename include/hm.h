@@ -282,8 +282,11 @@ hm_status hm_probe_random_access(uint64_t array_bytes, uint64_t ops, double *gop
  * hm_solve_host - one call from HOST buffers to HOST result: copies eoff,
  * pins, weights (host memory; pinned memory gives full link bandwidth) to
  * the device on `cuda_stream`, runs hm_create + hm_match + hm_result and
- * frees everything. Arguments as hm_create and hm_result (edges_out is
- * HOST int32[m] or NULL). Errors: union of those calls.
+ * frees everything. From 4M pins on, the pins cross in chunks on a second
+ * stream while the edge phase of the build runs; the call returns only
+ * after every copy has ended, so the caller may reuse its buffers at once.
+ * Arguments as hm_create and hm_result (edges_out is HOST int32[m] or
+ * NULL). Errors: union of those calls.
  */
 hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
                         const float *weights, uint64_t seed, uint32_t flags,

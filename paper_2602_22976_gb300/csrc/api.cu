@@ -397,7 +397,11 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
     // of the build (their validation, the order, the edge offsets) needs only
     // them and runs while the pins still cross the host link, in chunks, on a
     // second stream; each chunk is relabelled as soon as it has arrived.
+    // Below 4M pins (16 MB, under 0.1 ms on the link) the overlap saves less
+    // than the stream and events cost: the pins follow on the caller's stream
+    // and the build reads them from the device like hm_create.
     constexpr int kChunks = 8;
+    const bool chunked = kappa >= (int64_t)1 << 22;
     int64_t *d_eoff = nullptr;
     int32_t *d_pins = nullptr;
     float *d_w = nullptr;
@@ -408,19 +412,24 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
         const uint64_t x = (uint64_t)kappa * (uint64_t)c / kChunks;
         begin[c] = c == kChunks ? (uint64_t)kappa : x / kRelabelTile * kRelabelTile;
     }
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ew, cudaEventDisableTiming);
-    for (int c = 0; c < kChunks && e == cudaSuccess; ++c)
-        e = cudaEventCreateWithFlags(&ev_pins[c], cudaEventDisableTiming);
+    cudaError_t e = cudaSuccess;
+    if (chunked) {
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ew, cudaEventDisableTiming);
+        for (int c = 0; c < kChunks && e == cudaSuccess; ++c)
+            e = cudaEventCreateWithFlags(&ev_pins[c], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_eoff, (size_t)(m + 1) * 8, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_pins, (size_t)(kappa > 0 ? kappa : 1) * 4, s);
     if (e == cudaSuccess && weighted) e = cudaMallocAsync((void **)&d_w, (size_t)(m > 0 ? m : 1) * 4, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_eoff, eoff, (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && weighted && m > 0)
         e = cudaMemcpyAsync(d_w, weights, (size_t)m * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ev_ew, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_ew, 0);
-    for (int c = 0; c < kChunks && e == cudaSuccess; ++c) {
+    if (e == cudaSuccess && !chunked && kappa > 0)
+        e = cudaMemcpyAsync(d_pins, pins, (size_t)kappa * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && chunked) e = cudaEventRecord(ev_ew, s);
+    if (e == cudaSuccess && chunked) e = cudaStreamWaitEvent(cs, ev_ew, 0);
+    for (int c = 0; c < kChunks && e == cudaSuccess && chunked; ++c) {
         if (begin[c + 1] > begin[c])
             e = cudaMemcpyAsync(d_pins + begin[c], pins + begin[c], (size_t)(begin[c + 1] - begin[c]) * 4,
                                 cudaMemcpyHostToDevice, cs);
@@ -431,7 +440,8 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
     hm_handle *h = nullptr;
     if (st == HM_OK) {
         const PinChunks feed{kChunks, begin, ev_pins};
-        st = create_handle(&h, n, m, (uint64_t)kappa, d_eoff, d_pins, d_w, seed, weighted, s, &feed);
+        st = create_handle(&h, n, m, (uint64_t)kappa, d_eoff, d_pins, d_w, seed, weighted, s,
+                           chunked ? &feed : nullptr);
     }
     // the inputs are no longer needed once the handle is built; every copy
     // issued on the copy stream has finished before they are freed (on an

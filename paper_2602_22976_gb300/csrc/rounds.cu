@@ -570,11 +570,17 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
                     bool wr[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) wr[u] = jj[u] >= 0 && (!check || __ldcg(alive + jj[u]) != 0);
+                    if (check) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (wr[u])  // clear the flag byte with a reduction on its word
-                            atomicAnd(reinterpret_cast<unsigned int *>(alive) + (jj[u] >> 2),
-                                      ~(0xFFu << (8 * (jj[u] & 3))));
+                        for (int u = 0; u < 4; ++u)
+                            if (wr[u])  // clear the flag byte with a reduction on its word
+                                atomicAnd(reinterpret_cast<unsigned int *>(alive) + (jj[u] >> 2),
+                                          ~(0xFFu << (8 * (jj[u] & 3))));
+                    } else {  // round 1: every target, neighbours in the same word at once
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (wr[u]) alive[jj[u]] = 0;
+                    }
                 }
                 q = stop;
                 i += 32;

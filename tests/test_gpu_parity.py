@@ -191,9 +191,13 @@ def test_solve_host_matches_handle_path():
 
 
 def test_solve_host_graph_and_chunks():
-    """hm_solve_host on a graph (pairs gathered once every chunk of pins is
-    in) and on inputs smaller than one chunk of the upload."""
-    for h in (synth.rgg(seed=8, n=60_000), synth.small(seed=9, n=300, m=500),
+    """hm_solve_host on both sides of its 4M-pin split: above it the pins
+    cross in chunks beside the edge phase (a graph gathers its pairs once
+    every chunk is in), below it they follow the offsets on one stream."""
+    big = synth.large(seed=6, n=400_000, m=600_000)
+    big_graph = synth.rgg(seed=8, n=600_000)
+    assert big.kappa >= 1 << 22 and big_graph.kappa >= 1 << 22
+    for h in (big, big_graph, synth.rgg(seed=8, n=60_000), synth.small(seed=9, n=300, m=500),
               synth.from_edges(3, [[0, 1]], [0.5], seed=1)):
         o = oracle.match(h)
         r = hmlib.solve_host(h)
@@ -201,11 +205,12 @@ def test_solve_host_graph_and_chunks():
         assert r.weight == oracle.weight(h, o.in_matching)
 
 
-def test_solve_host_rejects_bad_input():
-    """hm_solve_host uploads the pins while the edge phase of the build runs:
-    a bad weight fails before the pins are used, a bad pin fails when they
-    arrive; both report HM_EINVAL, and the next call works."""
-    h = synth.large(seed=6, n=50_000, m=100_000)
+@pytest.mark.parametrize("n,m", [(50_000, 100_000), (400_000, 600_000)])
+def test_solve_host_rejects_bad_input(n, m):
+    """A bad weight fails before the pins are used, a bad pin fails when they
+    arrive (in its chunk above 4M pins, in the validation pass below); both
+    report HM_EINVAL, and the next call works."""
+    h = synth.large(seed=6, n=n, m=m)
     bad_w = synth.Hypergraph(h.n, h.m, h.eoff, h.pins, h.weights.copy(), h.seed)
     bad_w.weights[123] = -1.0
     r = hmlib.solve_host(bad_w, allow=(OK, EINVAL))
