@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
                 5: "HM_EBUSY"}
 HM_UNWEIGHTED, HM_BORROW_INPUT, HM_VALIDATE, HM_AUTOTUNE, HM_ONE_CLASS = 0x1, 0x2, 0x4, 0x8, 0x10
 HM_VERTEX_MATCHED, HM_VERTEX_NONE = -1, -2
-STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills", "items", "next", "live")
+STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills", "items", "next", "live", "deg")
 KERNELS = ("init", "argmax", "win", "kill", "round_end")
 
 # Every entry point of include/hm.h, in declaration order.

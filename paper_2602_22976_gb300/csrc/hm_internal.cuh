@@ -86,6 +86,7 @@ struct DevState {
     unsigned long long proposals;
     unsigned long long lpack;      // re-randomised rounds: (long lists << 32) | their chunks
     unsigned long long live;       // re-randomised rounds: live entries found by the scan
+    unsigned long long sdeg;       // fixed order, profiled rounds: degrees of the vertices kept
     unsigned long long kpack;      // kill ranges of the round: (entries << 32) | items
 };
 

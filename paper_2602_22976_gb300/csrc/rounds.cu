@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = st->live = st->kpack = 0;
+        st->lpack = st->live = st->kpack = st->sdeg = 0;
     }
 }
 
@@ -406,6 +406,27 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
     block_add_u64(props, s_red, &st->proposals);
 }
 
+// Statistics of the per-kernel replay only, launched between its timed
+// argmax and win kernels: the sum of the degrees of the vertices the argmax
+// step kept (the unmatched vertices with a live edge), added to the round's
+// counter. The timed match does not run it.
+__global__ void __launch_bounds__(kT) k_kept_degrees(RoundArgs a) {
+    __shared__ unsigned long long s_red[kT / 32];
+    DevState *st = a.st;
+    const int par = st->parity;
+    const int32_t *out = par ? a.list0 : a.list1;
+    const uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    unsigned long long sum = 0;
+    for (uint64_t g = warp; g < a.nregions; g += nwarps) {
+        const uint32_t c = cnt_out[g];
+        for (uint32_t i = lane; i < c; i += 32) sum += (uint32_t)a.vrec[out[g * a.region + i]].w;
+    }
+    block_add_u64(sum, s_red, &st->sdeg);
+}
+
 // a2: each warp takes 32 winners of the round at a time (warp_win). The
 // winners' vertex records were completed by the argmax kernel.
 __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
 __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t active, uint32_t nw,
                             uint32_t next, unsigned long long adv, unsigned long long props,
                             unsigned long long winpins, unsigned long long kills, uint32_t items,
-                            unsigned long long live) {
+                            unsigned long long live, unsigned long long sdeg) {
     if (r - 1 < kStatRounds) {
         int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
         row[HM_STAT_ACTIVE] = active;
@@ -442,6 +463,7 @@ __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t act
         row[HM_STAT_ITEMS] = items;
         row[HM_STAT_NEXT] = next;
         row[HM_STAT_LIVE] = (int64_t)live;
+        row[HM_STAT_DEG] = (int64_t)sdeg;
     }
     int cont = 0;
     if (st->fault) {
@@ -472,12 +494,12 @@ __device__ void round_end(const RoundArgs &a) {
     const int64_t active = r == 1 ? a.n : (int64_t)st->cnt[par];
     const unsigned long long kp = st->kpack;
     const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, kp >> 32,
-                                  (uint32_t)kp, st->live);
+                                  (uint32_t)kp, st->live, st->sdeg);
     st->nwin = 0;
     st->kdone = 0;
     st->rgrab = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
-    st->lpack = st->live = st->kpack = 0;
+    st->lpack = st->live = st->kpack = st->sdeg = 0;
     if (cont) {
         st->round = r + 1;
         st->parity = par ^ 1;
@@ -644,10 +666,16 @@ void launch_win_kill(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEv
     }
 }
 
-// One round of the fixed order. ev (or null): events 0-4 of a profiled round.
+// One round of the fixed order. ev (or null): events 0-5 of a profiled
+// round; the argmax span is ev[0] - ev[5], and the untimed degree count of
+// the kept vertices runs between it and the win span (ev[1] - ev[2]).
 void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
     k_argmax<<<h->argmax_grid, kT, 0, s>>>(a);
+    if (ev) {
+        cudaEventRecord(ev[5], s);
+        k_kept_degrees<<<grid_for((uint64_t)h->nregions * 32, kT, h->sm_count, 8), kT, 0, s>>>(a);
+    }
     launch_win_kill(h, a, s, ev, 1);
 }
 
@@ -908,7 +936,7 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "profile round");
         for (int k = 0; k < 4; ++k) {
-            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            cudaEventElapsedTime(&t, ev[k], k == 0 ? ev[5] : ev[k + 1]);
             ms[HM_K_ARGMAX + k] += t;
             launches[HM_K_ARGMAX + k] += k == 3 ? 0 : 1;  // the round end is part of the kill kernel
             if (r < max_rounds) round_ms[(int64_t)r * 4 + k] = t;

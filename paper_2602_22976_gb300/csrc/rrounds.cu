@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = st->live = st->kpack = 0;
+        st->lpack = st->live = st->kpack = st->sdeg = 0;
     }
 }
 

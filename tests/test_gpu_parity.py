@@ -323,6 +323,45 @@ def test_each_list_entry_touched_once():
         assert int(stats[:, adv].sum() + stats[:, kills].sum()) == h.kappa
 
 
+def _active_sets(h, o):
+    """From the oracle's run: for every round r, the vertices active at its
+    start (unmatched, with a live edge: some incident edge is decided in round
+    r or later) and the sum of their degrees."""
+    sizes = np.diff(h.eoff)
+    dec = o.decided_round.astype(np.int64)
+    vmax = np.zeros(h.n, dtype=np.int64)
+    np.maximum.at(vmax, h.pins, np.repeat(dec, sizes))
+    deg = np.bincount(h.pins, minlength=h.n)
+    return ([int((vmax >= r).sum()) for r in range(1, o.rounds + 1)],
+            [int(deg[vmax >= r].sum()) for r in range(1, o.rounds + 1)])
+
+
+def test_active_vertices_and_their_degrees_per_round():
+    """The argmax step's count of the vertices it keeps (HM_STAT_NEXT) and the
+    replay's count of their degrees (HM_STAT_DEG) equal, round by round, the
+    active vertex sets of the oracle's run and their degree sums. A plain
+    match leaves the degree column at 0."""
+    nxt = hmlib.STAT_COLUMNS.index("next")
+    dg = hmlib.STAT_COLUMNS.index("deg")
+    cases = [synth.large(seed=5, n=300_000, m=600_000), synth.small(seed=3),
+             synth.unweighted(seed=2, n=100_000, m=200_000), synth.rgg(seed=4, n=50_000),
+             synth.from_edges(7, [[0, 1], [1, 2], [2, 3], [3, 4]], None, seed=1)]
+    for h in cases:
+        o = oracle.match(h)
+        u, sdeg = _active_sets(h, o)
+        assert sdeg[0] == h.kappa
+        with hmlib.Matcher.from_hypergraph(h) as mt:
+            mt.match()
+            res = mt.result()
+            plain = mt.round_stats()
+            mt.profile()
+            stats = mt.round_stats()
+        assert res.status == OK and res.rounds == o.rounds
+        assert plain[:o.rounds, nxt].tolist() == u and not plain[:, dg].any()
+        assert stats[:o.rounds, nxt].tolist() == u
+        assert stats[:o.rounds, dg].tolist() == sdeg
+
+
 @pytest.mark.parametrize("big_weight", [1.0, 1e-3])
 def test_edge_wider_than_16_bit_counters(big_weight):
     """One edge of 70,000 pins: the P counters cannot be 16 bits wide, so the
