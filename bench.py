@@ -166,29 +166,42 @@ class Clocks:
 
 
 def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool = False,
-                 p16: bool = True) -> dict:
-    """Algorithmic bytes per kernel kind, summed over rounds (per-unit figures
-    in the design doc, section 6), from the per-round counters of hm_round_stats.
-    p16: the fixed order's P counters are 16 bits wide (every edge has at
-    most 65535 pins)."""
+                 p16: bool = True, pairs: bool = False) -> dict:
+    """Element bytes of this design per kernel kind, summed over rounds, from
+    the per-round counters of hm_round_stats. p16: the fixed order's P
+    counters are 16 bits wide (every edge has at most 65535 pins). pairs: a
+    graph in the fixed order (lists of {edge, other endpoint}, liveness from
+    the endpoints' matched flags, no kill step)."""
     ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT, LIVE = range(9)
     pc = 2 if p16 else 4  # bytes of one P counter
     if random:  # flags, two counter buffers, mask; records, offsets; list copy
         init = float(m * (1 + 4 + 4 + 1) + n * (16 + 16) + kappa * 8)
+    elif pairs:  # mask, P copied from its initial copy; matched flags
+        init = float(m * (1 + 2 * pc) + n)
     else:       # flag, mask, P copied from its initial copy (read + write)
         init = float(m * (1 + 1 + 2 * pc))
     b = {"init": init, "argmax": 0.0, "win": 0.0, "kill": 0.0, "round_end": 0.0}
     for r, row in enumerate(stats):
         row = row.astype(np.float64)
-        # winner: offset pair, order, mask, round; winner pin: pin, record read + write;
-        # kill range: item write
-        winb = row[WIN] * (16 + 4 + 1 + 4) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 8
+        if pairs:  # winner: order, mask; winner pin: pin, matched flag
+            winb = row[WIN] * (4 + 1) + row[WPIN] * (4 + 1)
+        else:  # winner: offset pair, order, mask; winner pin: pin, record read +
+               # write; kill range: item write
+            winb = row[WIN] * (16 + 4 + 1) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 8
         if random:  # list + record; scanned entry = entry + flag; live entry = id/base
                     # record + compacted write; proposal = record write, id map, offset
                     # pair, counter read+write, clear of the previous one; kept = list write
             b["argmax"] += (row[ACT] * ((4 if r else 0) + 16) + row[ADV] * (4 + 1)
                             + row[LIVE] * (8 + 4) + row[PROP] * (16 + 4 + 16 + 8 + 4)
                             + row[NEXT] * 4)
+        elif pairs:
+            if r == 0:  # first entry + its other endpoint + offset pair read, record write
+                b["argmax"] += row[ACT] * (4 + 4 + 16 + 16) + row[PROP] * 2 * pc + row[NEXT] * 4
+            else:       # list + record + matched flag; skipped entry = pair + flag;
+                        # proposal = record write + P read+write; kept vertex = list write
+                b["argmax"] += (row[ACT] * (4 + 16 + 1) + row[ADV] * (8 + 1)
+                                + row[PROP] * (16 + 2 * pc) + row[NEXT] * 4)
+            b["argmax"] += row[WIN] * (4 + 4 + 4)  # winner staged, read, listed
         else:
             if r == 0:  # first entry read + record (T, cursor) write; proposal =
                         # P read+write; kept vertex = list write
@@ -267,16 +280,17 @@ def kernel_source_hash(source: str = "rounds.cu") -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(step: str, randomised: bool) -> float | None:
+def measured_traffic(step: str, randomised: bool, workload: str = "large") -> float | None:
     """Per-launch DRAM bytes of a kernel step at the full bench size, read from
     the committed ncu summary (profiles/traffic.md) when the row was measured
-    on this source and in this mode (fixed order / re-randomised rounds)."""
+    on this source, in this mode (fixed order / re-randomised rounds) and on
+    this workload (the power-law instance unless the mode names another)."""
     p = os.path.join(ROOT, "profiles", "traffic.md")
     row, source = TRAFFIC_ROWS[(step, randomised)]
     if not os.path.exists(p):
         return None
     want = kernel_source_hash(source)
-    mode = "re-randomised" if randomised else "fixed"
+    mode = ("re-randomised" if randomised else "fixed") + ("" if workload == "large" else f", {workload}")
     for line in open(p):
         parts = [x.strip() for x in line.strip().strip("|").split("|")]
         if len(parts) >= 4 and parts[0] == row and parts[1] == mode and parts[2] == want:
@@ -567,7 +581,8 @@ def run_ours(args, world, rank, local):
     stats = mt.round_stats()
     create_ms = mt.create_ms()
     max_size = int(np.diff(h.eoff).max()) if h.m else 0
-    kb = kernel_bytes(stats, h.n, h.m, h.kappa, rnd_mode, p16=max_size <= 0xFFFF)
+    pairs = not rnd_mode and h.m > 0 and max_size == 2 and h.kappa == 2 * h.m  # a graph
+    kb = kernel_bytes(stats, h.n, h.m, h.kappa, rnd_mode, p16=max_size <= 0xFFFF, pairs=pairs)
     dom = max(("argmax", "win", "kill"), key=lambda k: prof[k][0])
     assert all(isinstance(prof[k], tuple) for k in hm.KERNELS)
     peaks = measured_peaks()
@@ -689,7 +704,7 @@ def run_ours(args, world, rank, local):
                                     "p99": float(np.percentile(step_ms, 99))},
             "create_ms": create_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, rnd_mode),
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, rnd_mode, args.workload),
                          "alg_bytes_per_launch": alg_bytes / max(1, prof[dom][1]), "bytes_model": bytes_model,
                          "design_bytes_per_launch": kb[dom] / max(1, prof[dom][1]),
                          "design_frac": design_gbs / peaks["hbm_gbs"],

@@ -208,7 +208,9 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
 #define HM_STAT_PROPOSALS 2  /* vertices that chose a new best edge */
 #define HM_STAT_WINNERS   3  /* edges that joined M */
 #define HM_STAT_WINPINS   4  /* sum of |e| over those edges */
-#define HM_STAT_KILLS     5  /* adjacency entries deactivated by the kill step */
+#define HM_STAT_KILLS     5  /* adjacency entries deactivated by the kill step (0 for
+                                graphs in the fixed order, which read an edge's
+                                liveness from its endpoints and have no kill step) */
 #define HM_STAT_ITEMS     6  /* kill ranges (one per newly matched vertex) */
 #define HM_STAT_NEXT      7  /* vertices kept for the next round */
 #define HM_STAT_LIVE      8  /* re-randomised rounds: live entries the argmax scan

@@ -182,6 +182,7 @@ hm_status build_class(Batch *b, BatchClass &c, const int64_t *eoff, const int32_
     }
     if (st == HM_OK) {
         Handle *h = new (std::nothrow) Handle();
+        if (h) h->edge_rounds = true;  // an instance's round count is the round of its last winner
         if (!h) {
             st = HM_ENOMEM;
         } else {

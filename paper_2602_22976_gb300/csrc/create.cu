@@ -287,12 +287,36 @@ __global__ void k_voff(const uint32_t *__restrict__ sv, const uint32_t *__restri
 }
 
 // Constant half of the per-vertex record: list start and degree (the
-// mutable half, T[v] and its cursor, is reset by every match).
-__global__ void k_vrec_meta(const int64_t *__restrict__ voff, int64_t n, int4 *__restrict__ vrec) {
+// mutable half, T[v] and its cursor, is reset by every match). Graphs keep
+// {T[v], cursor, list end, other endpoint of T[v]}, all rewritten by round 1.
+__global__ void k_vrec_meta(const int64_t *__restrict__ voff, int64_t n, int graph, int4 *__restrict__ vrec,
+                            int32_t *__restrict__ firstnbr) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = voff[v], e = voff[v + 1];
-        vrec[v] = make_int4(-2, 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
+        if (graph) {
+            vrec[v] = make_int4(-2, (int32_t)(uint32_t)b, (int32_t)(uint32_t)e, -1);
+            if (e == b) firstnbr[v] = -1;
+        } else {
+            vrec[v] = make_int4(-2, 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
+        }
+    }
+}
+
+// Graphs: each list entry with the other endpoint of its edge (vertex key[p]
+// owns entry p, edge vadj[p] has pins pinsj[2j], pinsj[2j + 1]), and that
+// endpoint for every list's first entry.
+__global__ void k_pairs_nbr(const uint32_t *__restrict__ key, const int32_t *__restrict__ vadj,
+                            const int32_t *__restrict__ pinsj, uint64_t kappa, int2 *__restrict__ vpair,
+                            int32_t *__restrict__ firstnbr) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < kappa;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = key[p];
+        const int32_t j = vadj[p];
+        const int2 e = __ldg(reinterpret_cast<const int2 *>(pinsj) + j);
+        const int32_t o = (uint32_t)e.x == v ? e.y : e.x;
+        vpair[p] = make_int2(j, o);
+        if (p == 0 || key[p - 1] != v) firstnbr[v] = o;
     }
 }
 
@@ -510,13 +534,20 @@ hm_status create_structures(Handle *h, const int64_t *eoff, const int32_t *pins,
         (st = dalloc(&h->firstj, (uint64_t)n, s, "first entries")) != HM_OK ||
         (st = dalloc(&h->vrec, (uint64_t)n, s, "vertex records")) != HM_OK)
         return st;
+    if (h->graph && ((st = dalloc(&h->vpair, kappa, s, "list pairs")) != HM_OK ||
+                     (st = dalloc(&h->firstnbr, (uint64_t)n, s, "first neighbours")) != HM_OK))
+        return st;
     const int vbits = bit_width(n > 0 ? (uint64_t)(n - 1) : 0);
     ce = radix_sort_pairs((const uint32_t *)h->pinsj, val, key, (uint32_t *)h->vadj, tk, tv, kappa,
                           vbits, rscratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "vertex sort");
     k_voff<<<grid_for(kappa + 1, kT, h->sm_count, 16), kT, 0, s>>>(key, (const uint32_t *)h->vadj,
                                                                   kappa, n, h->voff, h->firstj, derr);
-    k_vrec_meta<<<grid_for((uint64_t)n, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, n, h->vrec);
+    if (h->graph && kappa)
+        k_pairs_nbr<<<grid_for(kappa, kT, h->sm_count, 16), kT, 0, s>>>(key, h->vadj, h->pinsj, kappa, h->vpair,
+                                                                       h->firstnbr);
+    k_vrec_meta<<<grid_for((uint64_t)n, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, n, h->graph ? 1 : 0, h->vrec,
+                                                                         h->firstnbr);
     cudaEventRecord(ev.e[4], s);
     cudaMemcpyAsync(&herr, derr, sizeof herr, cudaMemcpyDeviceToHost, s);
     ce = cudaStreamSynchronize(s);

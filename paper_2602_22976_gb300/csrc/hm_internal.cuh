@@ -23,6 +23,15 @@
 //                       load serves both the liveness check and the advance.
 //   firstj int32[n]     first entry of every vertex list (T[v] of round 1; round
 //                       1 writes T and the cursor of every record from it)
+//   graphs (every edge has two pins), fixed order: an edge is live exactly
+//   when neither endpoint is matched, so liveness is read from the vertices
+//   and there is no kill step:
+//   vpair  int2[kappa]  {edge j, other endpoint} of every list entry, in vadj's
+//                       order
+//   firstnbr int32[n]   other endpoint of every vertex's first entry
+//   vmatch uint8[n]     1 once the vertex is covered by M
+//   vrec   int4[n]      {T[v], cursor (absolute position), list end, other
+//                       endpoint of T[v]} instead of the layout above
 //   list0/list1 int32[nregions*region] active vertex lists (ping-pong). The
 //                       list is cut into one region per warp of the argmax
 //                       grid; region g holds the active vertices of the
@@ -38,7 +47,8 @@
 //                       range in the round's concatenation of all ranges},
 //                       the offsets ascending with the item index
 //   wround int32[m]     round in which an edge joined M (input numbering; only
-//                       read for matched edges)
+//                       read for matched edges; batches only, which report
+//                       each instance's round count)
 //   inM    uint8[m]     result mask, input numbering
 #pragma once
 
@@ -111,6 +121,10 @@ struct RoundArgs {
     const uint32_t *P0;    // initial P words (built once per handle)
     int4 *vrec;
     const int32_t *firstj;
+    int pairs;             // graph, fixed order: liveness from vmatch, no kill step
+    const int2 *vpair;     // pairs: {edge, other endpoint} per list entry
+    const int32_t *firstnbr;
+    uint8_t *vmatch;
     int32_t *list0;
     int32_t *list1;
     uint32_t *lcnt;
@@ -165,6 +179,9 @@ struct Handle {
     uint32_t *P0 = nullptr;     // initial P words
     int4 *vrec = nullptr;
     int32_t *firstj = nullptr;
+    int2 *vpair = nullptr;      // graphs: {edge, other endpoint} per list entry
+    int32_t *firstnbr = nullptr;
+    uint8_t *vmatch = nullptr;  // graphs: matched flag per vertex
     int32_t *list0 = nullptr, *list1 = nullptr;
     uint32_t *lcnt = nullptr;
     int32_t *wstage = nullptr;
@@ -173,7 +190,8 @@ struct Handle {
     uint32_t regions_cap = 0;  // entries per parity in lcnt
     unsigned argmax_grid = 0, win_grid = 0, kill_grid = 0;
     LaunchConfig cfg, graph_cfg;
-    int32_t *wround = nullptr;
+    bool edge_rounds = false;   // keep each matched edge's round (batches: rounds per instance)
+    int32_t *wround = nullptr;  // allocated when edge_rounds
     // re-randomised rounds (allocated on first use, rrounds.cu)
     float noise = 0.f;          // 0: fixed order; > 0: amplitude of the per-round noise
     float graph_noise = 0.f;    // amplitude exec_rand was built with

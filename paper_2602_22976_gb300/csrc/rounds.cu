@@ -22,6 +22,11 @@
 // The active vertex list is compacted inside k_argmax (vertices that are
 // matched or have no live edge left drop out), each warp in place in its own
 // region of the list.
+// Graphs (every edge has two pins) skip the kill: an edge is live exactly
+// when neither endpoint is matched, so k_argmax reads each list entry with
+// its other endpoint and that endpoint's matched flag, k_win only sets the
+// flags of the winners' endpoints, and the kill step is one block that ends
+// the round.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -68,15 +73,19 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
     __syncthreads();
 }
 
-// Per-match reset: live flags, result mask, and the P counters from their
-// initial copy (P0). The vertex records' T and cursor are set by round 1.
+// Per-match reset: live flags (matched flags of the vertices for graphs),
+// result mask, and the P counters from their initial copy (P0). The vertex
+// records' T and cursor are set by round 1.
 __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
     const int64_t pw = a.p16 ? (a.m + 1) / 2 : a.m;  // words of P
     for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < a.m; i += (int64_t)gridDim.x * kT) {
-        a.alive[i] = 1;
+        if (!a.pairs) a.alive[i] = 1;
         a.inM[i] = 0;
         if (i < pw) a.P[i] = __ldg(a.P0 + i);
     }
+    if (a.pairs)
+        for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kT)
+            a.vmatch[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevState *st = a.st;
         st->round = 1;
@@ -143,40 +152,84 @@ __device__ __forceinline__ int64_t next_live_bounded(const int32_t *__restrict__
     return c >= end ? end : -1;
 }
 
+// The same walk over a graph's pair list: entry c is live when the other
+// endpoint of its edge is unmatched (the list's own vertex is active, so it
+// is unmatched too). Returns the position, with j = the edge and o = that
+// endpoint; end or -1 as above.
+__device__ __forceinline__ int64_t next_live_pair(const int2 *__restrict__ vpair, const uint8_t *__restrict__ vmatch,
+                                                  int64_t c, int64_t end, int32_t &j, int32_t &o) {
+#pragma unroll 1
+    for (int step = 0; step < kLaneSteps; ++step) {
+        if (c >= end) return end;
+        const int2 e0 = __ldg(vpair + c);
+        const int2 e1 = c + 1 < end ? __ldg(vpair + c + 1) : make_int2(-1, -1);
+        const int2 e2 = c + 2 < end ? __ldg(vpair + c + 2) : make_int2(-1, -1);
+        const int2 e3 = c + 3 < end ? __ldg(vpair + c + 3) : make_int2(-1, -1);
+        const bool a0 = __ldg(vmatch + e0.y) == 0;
+        const bool a1 = e1.y >= 0 && __ldg(vmatch + e1.y) == 0;
+        const bool a2 = e2.y >= 0 && __ldg(vmatch + e2.y) == 0;
+        const bool a3 = e3.y >= 0 && __ldg(vmatch + e3.y) == 0;
+        if (a0) { j = e0.x; o = e0.y; return c; }
+        if (a1) { j = e1.x; o = e1.y; return c + 1; }
+        if (a2) { j = e2.x; o = e2.y; return c + 2; }
+        if (a3) { j = e3.x; o = e3.y; return c + 3; }
+        c += 4;
+    }
+    return c >= end ? end : -1;
+}
+
 // a1 for one vertex per lane: T[v] <- the first live entry of v's list at
 // or after its cursor. Returns whether v stays active; nb = the edge v newly
 // chose (it must count down P[nb]) or -1. All 32 lanes must call it: a lane
 // whose walk exceeds its budget is finished by the whole warp, 32 entries
-// per step (coalesced list read, one ballot).
+// per step (coalesced list read, one ballot). kPairs: a graph's lists of
+// {edge, other endpoint}, liveness read from the endpoints' matched flags,
+// records {T, absolute cursor, list end, other endpoint of T}.
+template <bool kPairs>
 __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok, int32_t v, int32_t &nb,
                                               unsigned long long &adv) {
     const int lane = threadIdx.x & 31;
     const int32_t *__restrict__ vadj = a.vadj;
+    const int2 *__restrict__ vpair = a.vpair;
     const uint8_t *__restrict__ alive = a.alive;
+    const uint8_t *__restrict__ vmatch = a.vmatch;
     bool keep = false, walk = false, coop = false;
     nb = -1;
     int64_t vb = 0, from = 0, end = 0, cn = 0;
-    int32_t jj = 0;
+    int32_t jj = 0, oo = 0;
     if (ok && r == 1) {
         // every edge is live in round 1: T[v] is the first entry; the record
         // (T, cursor) starts here
         const int32_t f = __ldg(a.firstj + v);
-        reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(f, 0);
+        if (kPairs)
+            a.vrec[v] = make_int4(f, (int32_t)(uint32_t)__ldg(a.voff + v), (int32_t)(uint32_t)__ldg(a.voff + v + 1),
+                                  __ldg(a.firstnbr + v));
+        else
+            reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(f, 0);
         if (f >= 0) {
             nb = f;
             keep = true;
         }
     } else if (ok) {
+        // graphs: a matched vertex keeps its record; its own flag, loaded
+        // beside the record, says so
+        const bool mine = kPairs && __ldg(vmatch + v) != 0;
         const int4 rec = a.vrec[v];
-        if (rec.x >= 0) {
-            if (__ldg(alive + rec.x)) {
+        if (rec.x >= 0 && !mine) {
+            if (kPairs ? __ldg(vmatch + rec.w) == 0 : __ldg(alive + rec.x) != 0) {
                 keep = true;  // T[v] still live: unchanged
             } else {
-                vb = (int64_t)(uint32_t)rec.z;
-                end = vb + (int64_t)(uint32_t)rec.w;
-                from = vb + rec.y;
+                if (kPairs) {
+                    from = (int64_t)(uint32_t)rec.y;
+                    end = (int64_t)(uint32_t)rec.z;
+                    cn = next_live_pair(vpair, vmatch, from + 1, end, jj, oo);
+                } else {
+                    vb = (int64_t)(uint32_t)rec.z;
+                    end = vb + (int64_t)(uint32_t)rec.w;
+                    from = vb + rec.y;
+                    cn = next_live_bounded(vadj, alive, from + 1, end, jj);
+                }
                 walk = true;
-                cn = next_live_bounded(vadj, alive, from + 1, end, jj);
                 coop = cn < 0;
             }
         }
@@ -187,15 +240,25 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
         int64_t p = __shfl_sync(kFull, from, src) + 1 + 4 * kLaneSteps;
         const int64_t e = __shfl_sync(kFull, end, src);
         int64_t fpos = e;
-        int32_t fj = 0;
+        int32_t fj = 0, fo = 0;
         while (p < e) {
             const int64_t q = p + lane;
-            const int32_t ej = q < e ? __ldg(vadj + q) : -1;
-            const unsigned lm = __ballot_sync(kFull, ej >= 0 && __ldg(alive + ej) != 0);
+            unsigned lm;
+            int32_t ej, eo = 0;
+            if (kPairs) {
+                const int2 x = q < e ? __ldg(vpair + q) : make_int2(-1, -1);
+                ej = x.x;
+                eo = x.y;
+                lm = __ballot_sync(kFull, eo >= 0 && __ldg(vmatch + eo) == 0);
+            } else {
+                ej = q < e ? __ldg(vadj + q) : -1;
+                lm = __ballot_sync(kFull, ej >= 0 && __ldg(alive + ej) != 0);
+            }
             if (lm) {
                 const int f = __ffs(lm) - 1;
                 fpos = p + f;
                 fj = __shfl_sync(kFull, ej, f);
+                if (kPairs) fo = __shfl_sync(kFull, eo, f);
                 break;
             }
             p += 32;
@@ -203,10 +266,20 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
         if (lane == src) {
             cn = fpos;
             jj = fj;
+            oo = fo;
         }
         cm &= cm - 1;
     }
-    if (walk) {
+    if (walk && kPairs) {
+        adv += (unsigned long long)(cn - from);
+        if (cn < end) {
+            a.vrec[v] = make_int4(jj, (int32_t)(uint32_t)cn, (int32_t)(uint32_t)end, oo);
+            nb = jj;
+            keep = true;
+        } else {
+            a.vrec[v] = make_int4(kCurNone, 0, 0, -1);
+        }
+    } else if (walk) {
         adv += (unsigned long long)(cn - from);
         int2 *st2 = reinterpret_cast<int2 *>(a.vrec + v);
         if (cn < end) {
@@ -245,9 +318,18 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
         }
         const int32_t ein = __ldg(a.order + j);
         a.inM[ein] = 1;
-        a.wround[ein] = r;
+        if (a.wround) a.wround[ein] = r;
         winpins += len;
+        if (a.pairs) {
+            // graph, fixed order: both endpoints chose j (the countdown
+            // reached 0); their matched flags are the whole update - the
+            // argmax step reads them, and there is no kill range
+            const int2 e = __ldg(reinterpret_cast<const int2 *>(a.pinsj) + j);
+            a.vmatch[e.x] = 1;
+            a.vmatch[e.y] = 1;
+        }
     }
+    if (a.pairs) return;
     const uint32_t inc = warp_inclusive_scan(len);
     const uint32_t exc = inc - len;
     const uint32_t total = __shfl_sync(kFull, inc, 31);
@@ -326,6 +408,7 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
 // warps' winners and copies them into the contiguous winner list (k_win
 // reads the winners' vertex records, which must be complete: that is what
 // keeps a2 in its own kernel).
+template <bool kPairs>
 __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     __shared__ uint32_t s_keep[kT / 32], s_won[kT / 32];
@@ -356,7 +439,7 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
             const bool ok = i < count;
             const int32_t v = ok ? (r == 1 ? (int32_t)(base + i) : in[base + i]) : 0;
             int32_t nb;
-            const bool keep = argmax_vertex(a, r, ok, v, nb, adv);
+            const bool keep = argmax_vertex<kPairs>(a, r, ok, v, nb, adv);
             bool w = false;
             if (nb >= 0) {
                 ++props;
@@ -422,7 +505,10 @@ __global__ void __launch_bounds__(kT) k_kept_degrees(RoundArgs a) {
     unsigned long long sum = 0;
     for (uint64_t g = warp; g < a.nregions; g += nwarps) {
         const uint32_t c = cnt_out[g];
-        for (uint32_t i = lane; i < c; i += 32) sum += (uint32_t)a.vrec[out[g * a.region + i]].w;
+        for (uint32_t i = lane; i < c; i += 32) {
+            const int32_t v = out[g * a.region + i];
+            sum += a.pairs ? (uint32_t)a.vrec[v].z - (uint64_t)a.voff[v] : (uint32_t)a.vrec[v].w;
+        }
     }
     block_add_u64(sum, s_red, &st->sdeg);
 }
@@ -623,10 +709,13 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
     }
 }
 
-__global__ void k_vertex_state(const int4 *vrec, const int32_t *order, int64_t n, int32_t *out) {
+// vmatch (graphs in the fixed order, else null): the matched flags, which
+// there stand in for T[v] = kCurMatched.
+__global__ void k_vertex_state(const int4 *vrec, const uint8_t *vmatch, const int32_t *order, int64_t n,
+                               int32_t *out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t j = vrec[v].x;
+        const int32_t j = vmatch && vmatch[v] ? kCurMatched : vrec[v].x;
         out[v] = j >= 0 ? order[j] : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
     }
 }
@@ -650,8 +739,14 @@ unsigned grid_of(const Handle *h, K kernel, int want) {
     return (unsigned)std::max(1, h->sm_count * b);
 }
 
+// The argmax kernel a handle runs: graphs read liveness from their pair lists.
+void (*argmax_kernel(const Handle *h))(RoundArgs) {
+    return h->graph ? k_argmax<true> : k_argmax<false>;
+}
+
 void launch_kill(const Handle *h, const RoundArgs &a, cudaStream_t s, int kill_stride) {
     if (kill_stride == 2) k_kill<2><<<h->kill_grid, kT, 0, s>>>(a);
+    else if (a.pairs) k_kill<1><<<1, kT, 0, s>>>(a);  // nothing to kill: one block ends the round
     else k_kill<1><<<h->kill_grid, kT, 0, s>>>(a);
 }
 
@@ -671,7 +766,8 @@ void launch_win_kill(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEv
 // the kept vertices runs between it and the win span (ev[1] - ev[2]).
 void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
-    k_argmax<<<h->argmax_grid, kT, 0, s>>>(a);
+    if (a.pairs) k_argmax<true><<<h->argmax_grid, kT, 0, s>>>(a);
+    else k_argmax<false><<<h->argmax_grid, kT, 0, s>>>(a);
     if (ev) {
         cudaEventRecord(ev[5], s);
         k_kept_degrees<<<grid_for((uint64_t)h->nregions * 32, kT, h->sm_count, 8), kT, 0, s>>>(a);
@@ -806,6 +902,10 @@ RoundArgs round_args(const Handle *h) {
     a.P0 = h->P0;
     a.vrec = h->vrec;
     a.firstj = h->firstj;
+    a.pairs = h->graph ? 1 : 0;
+    a.vpair = h->vpair;
+    a.firstnbr = h->firstnbr;
+    a.vmatch = h->vmatch;
     a.list0 = h->list0;
     a.list1 = h->list1;
     a.lcnt = h->lcnt;
@@ -842,16 +942,17 @@ hm_status alloc_round_state(Handle *h, cudaStream_t s) {
         return HM_EINVAL;
     }
     // list regions: sized for the largest argmax grid any launch config can use
-    h->regions_cap = (uint32_t)(h->sm_count * max_blocks_per_sm(k_argmax) * (kT / 32));
+    h->regions_cap = (uint32_t)(h->sm_count * max_blocks_per_sm(argmax_kernel(h)) * (kT / 32));
     h->list_cap = n + 32 * (uint64_t)h->regions_cap + 32;
     if ((st = dalloc(&h->list0, h->list_cap, s, "active list")) != HM_OK) return st;
     if ((st = dalloc(&h->list1, h->list_cap, s, "active list")) != HM_OK) return st;
     if ((st = dalloc(&h->wstage, h->list_cap, s, "winner staging")) != HM_OK) return st;
     if ((st = dalloc(&h->lcnt, 2 * (uint64_t)h->regions_cap, s, "region lengths")) != HM_OK) return st;
-    if ((st = dalloc(&h->wround, m, s, "win rounds")) != HM_OK) return st;
+    if (h->edge_rounds && (st = dalloc(&h->wround, m, s, "win rounds")) != HM_OK) return st;
     if ((st = dalloc(&h->win, h->win_cap, s, "winners")) != HM_OK) return st;
     if ((st = dalloc(&h->items, h->item_cap, s, "kill items")) != HM_OK) return st;
     if ((st = dalloc(&h->inM, m, s, "result mask")) != HM_OK) return st;
+    if (h->graph && (st = dalloc(&h->vmatch, n, s, "matched flags")) != HM_OK) return st;
     if ((st = apply_config(h, h->cfg)) != HM_OK) return st;
     if (m) {
         RoundArgs a = round_args(h);
@@ -882,7 +983,7 @@ hm_status apply_config(Handle *h, const LaunchConfig &c) {
         return HM_EINVAL;
     }
     h->cfg = c;
-    h->argmax_grid = grid_of(h, k_argmax, c.argmax_bpsm);
+    h->argmax_grid = grid_of(h, argmax_kernel(h), c.argmax_bpsm);
     h->win_grid = grid_of(h, k_win, c.win_bpsm);
     h->kill_grid = grid_of(h, k_kill<1>, c.kill_bpsm);
     h->nregions = h->argmax_grid * (kT / 32);
@@ -990,7 +1091,7 @@ hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_m
         }
         return HM_OK;
     };
-    const int fit_arg = max_blocks_per_sm(k_argmax);
+    const int fit_arg = max_blocks_per_sm(argmax_kernel(h));
     for (int pass = 0; pass < 2 && st == HM_OK; ++pass) {
         for (int chunk : {64, 128, 256, 512, 1024}) {
             LaunchConfig c = cur;
@@ -1021,7 +1122,9 @@ hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_m
 
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
     const int4 *vrec = h->last_random ? h->vrecR : h->vrec;
-    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(vrec, h->order, h->n, out_dev);
+    const uint8_t *vmatch = h->last_random ? nullptr : h->vmatch;  // set for graphs only
+    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(vrec, vmatch, h->order, h->n,
+                                                                               out_dev);
     return cudaGetLastError();
 }
 
@@ -1030,7 +1133,7 @@ cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t 
 void free_handle_buffers(Handle *h) {
     free_rand_buffers(h);
     void *bufs[] = {h->voff, h->vadj, h->eoffj, h->pinsj, h->order, h->weights, h->alive, h->P, h->P0,
-                    h->vrec, h->firstj, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win,
+                    h->vrec, h->firstj, h->vpair, h->firstnbr, h->vmatch, h->list0, h->list1, h->lcnt, h->wstage, h->wround, h->win,
                     h->items, h->inM, h->stats, h->st, h->res_idx, h->res_w, h->res_part, h->res_bucket};
     cudaStream_t s = h->cap_stream;
     for (void *p : bufs)

@@ -460,6 +460,7 @@ int fit_per_sm(K kernel) {
 RoundArgs rand_args(const Handle *h) {
     RoundArgs a = round_args(h);
     a.vrec = h->vrecR;
+    a.pairs = 0;  // the re-randomised rounds keep their own lists and kill step
     a.vadj = reinterpret_cast<const int32_t *>(h->vadjR);  // for the kill step: stride 2
     a.vadjE = h->vadjE;
     a.vadjR = h->vadjR;

@@ -315,12 +315,42 @@ def test_each_list_entry_touched_once():
     adv = hmlib.STAT_COLUMNS.index("advance")
     kills = hmlib.STAT_COLUMNS.index("kills")
     cases = [synth.large(seed=5, n=300_000, m=600_000), synth.small(seed=3),
-             synth.unweighted(seed=2, n=100_000, m=200_000),
-             synth.from_edges(5, [[0, 1], [1, 2], [2, 3], [3, 4]], None, seed=1)]
+             synth.unweighted(seed=2, n=100_000, m=200_000)]
     for h in cases:
         res, stats, _ = run_gpu(h)
         assert res.status == OK
         assert int(stats[:, adv].sum() + stats[:, kills].sum()) == h.kappa
+
+
+def _entries_ahead_of_the_match(h, o):
+    """Over a whole run, the cursor of a vertex passes exactly the entries of
+    its list that rank above its matching edge, or its whole list if it stays
+    unmatched: summed over the vertices, from the oracle's matching."""
+    keys = oracle.keys(h)
+    eid = np.repeat(np.arange(h.m), np.diff(h.eoff))
+    mv = np.full(h.n, -1, dtype=np.int64)
+    won = o.in_matching[eid] == 1
+    mv[h.pins[won]] = eid[won]
+    matched = mv >= 0
+    ahead = matched[h.pins] & (keys[eid] > keys[np.maximum(mv[h.pins], 0)])
+    return int(ahead.sum()) + int(np.bincount(h.pins, minlength=h.n)[~matched].sum())
+
+
+def test_graph_cursors_pass_each_entry_once():
+    """Graphs run without a kill step (an edge is live while neither endpoint
+    is matched): the kill counter stays 0, and the entries the cursors skip
+    are exactly those ahead of each vertex's matching edge."""
+    adv = hmlib.STAT_COLUMNS.index("advance")
+    kills = hmlib.STAT_COLUMNS.index("kills")
+    cases = [synth.rgg(seed=5, n=80_000), synth.rgg(seed=6, n=20_000, avg_degree=40),
+             synth.from_edges(5, [[0, 1], [1, 2], [2, 3], [3, 4]], None, seed=1),
+             synth.from_edges(6, [[0, 1], [0, 2], [0, 3], [4, 5]], [1.0, 3.0, 2.0, 1.0], seed=1)]
+    for h in cases:
+        res, stats, _ = run_gpu(h)
+        o = oracle.match(h)
+        assert res.status == OK and np.array_equal(res.edges, o.edges) and res.rounds == o.rounds
+        assert not stats[:, kills].any()
+        assert int(stats[:, adv].sum()) == _entries_ahead_of_the_match(h, o)
 
 
 def _active_sets(h, o):
