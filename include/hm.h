@@ -293,6 +293,10 @@ hm_status hm_probe_random_access(uint64_t array_bytes, uint64_t ops, double *gop
  * frees everything. From 4M pins on, the pins cross in chunks on a second
  * stream while the edge phase of the build runs; the call returns only
  * after every copy has ended, so the caller may reuse its buffers at once.
+ * Up to 2^17 pins with no edge above 256 pins, one thread block runs the
+ * whole matching instead (same matching, rounds, weight and errors; its
+ * working memory comes from the stream's pool, so concurrent calls are
+ * safe), which saves the build and graph costs of a handle.
  * Arguments as hm_create and hm_result (edges_out is HOST int32[m] or
  * NULL). Errors: union of those calls.
  */

@@ -2,6 +2,7 @@
 #include "hm_internal.cuh"
 #include "exact_sum.cuh"
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -393,6 +394,23 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
     int dev = 0;
     cudaGetDevice(&dev);
     raise_pool_threshold(dev);
+    if (m == 0) {
+        if (count_out) *count_out = 0;
+        if (rounds_out) *rounds_out = 0;
+        if (weight_out) *weight_out = 0.0;
+        return HM_OK;
+    }
+    // Small inputs: one thread block runs the whole matching (a handle's
+    // build, graph and their synchronisations cost more than the matching
+    // there). Its repeated-vertex check compares pairs within an edge, so
+    // it takes inputs whose edges are at most kSmallMaxSize pins.
+    if ((uint64_t)kappa <= kSmallPins) {
+        int64_t widest = 0;
+        for (int64_t e = 0; e < m; ++e) widest = std::max(widest, eoff[e + 1] - eoff[e]);
+        if (widest <= kSmallMaxSize)
+            return solve_small(n, m, (uint64_t)kappa, eoff, pins, weights, seed, weighted, edges_out, count_out,
+                               rounds_out, weight_out, s);
+    }
     // The offsets and weights go first on the caller's stream: the edge phase
     // of the build (their validation, the order, the edge offsets) needs only
     // them and runs while the pins still cross the host link, in chunks, on a

@@ -262,6 +262,14 @@ cudaError_t weight_buckets(const uint8_t *flags, const float *w, uint64_t n, uns
 cudaError_t compact_flags(const uint8_t *flags, uint64_t n, const float *w, int32_t *idx_out,
                           float *w_out, uint32_t *part, cudaStream_t s);
 
+// hm_solve_host below kSmallPins pins (every edge at most kSmallMaxSize
+// pins): one thread block runs the whole matching (noalloc.cu).
+constexpr uint64_t kSmallPins = uint64_t(1) << 17;
+constexpr int64_t kSmallMaxSize = 256;
+hm_status solve_small(int64_t n, int64_t m, uint64_t kappa, const int64_t *eoff, const int32_t *pins,
+                      const float *weights, uint64_t seed, bool weighted, int32_t *edges_out,
+                      int64_t *count_out, int32_t *rounds_out, double *weight_out, cudaStream_t s);
+
 // ---- create (create.cu) ----
 // inst_ebase (device, ninst entries): first edge of each instance when the
 // input is a union of independent instances (local hash priorities), else null.

@@ -205,6 +205,63 @@ def test_solve_host_graph_and_chunks():
         assert r.weight == oracle.weight(h, o.in_matching)
 
 
+def _small_cases():
+    rng = np.random.default_rng(11)
+    hub = [[0, int(v)] for v in rng.permutation(np.arange(1, 3000))[:2000]]  # a hub of degree 2000
+    wide = [list(range(1500))] + [[int(a), int(a) + 1] for a in range(1500, 1600)]  # one 1500-pin edge
+    return [synth.small(seed=9, n=300, m=500), synth.small(seed=3),
+            synth.serve_request(1000, seed=1), synth.serve_request(30_000, seed=2),
+            synth.serve_request(120_000, seed=3), synth.unweighted(seed=4, n=5000, m=10_000),
+            synth.rgg(seed=5, n=6000), synth.from_edges(3, [[0, 1]], [0.5], seed=1),
+            synth.from_edges(3000, hub, list(rng.random(len(hub), dtype=np.float32) + 0.01), seed=2),
+            synth.from_edges(1700, wide, None, seed=3)]
+
+
+@pytest.mark.parametrize("i", range(10))
+def test_solve_host_small_inputs(i):
+    """hm_solve_host below 2^17 pins runs the whole matching in one thread
+    block (edges of at most 256 pins; the 1500-pin edge of the last case
+    takes the handle path): the same matching, round count and exact weight
+    as the oracle."""
+    h = _small_cases()[i]
+    assert h.kappa <= 1 << 17
+    o = oracle.match(h)
+    r = hmlib.solve_host(h)
+    assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+    assert r.weight == oracle.weight(h, o.in_matching)
+
+
+def test_solve_host_small_rejects_bad_input():
+    """The one-block path rejects what hm_create rejects, with the same
+    messages: an empty edge, a pin outside [0, n), a weight that is not
+    finite and > 0, and a vertex twice in one edge (short edges, and edges
+    longer than 16 pins, which a warp checks); the next call works."""
+    h = synth.serve_request(20_000, seed=4)
+    sizes = np.diff(h.eoff)
+    long_e = int(np.flatnonzero(sizes > 40)[0])
+    short_e = int(np.flatnonzero(sizes == 3)[0])
+
+    def bad(mutate, word):
+        x = synth.Hypergraph(h.n, h.m, h.eoff.copy(), h.pins.copy(), h.weights.copy(), h.seed)
+        mutate(x)
+        r = hmlib.solve_host(x, allow=(OK, EINVAL))
+        assert r.status == EINVAL and word in hmlib.last_error(), hmlib.last_error()
+
+    bad(lambda x: x.weights.__setitem__(17, -0.0), "weight of edge 17")
+    bad(lambda x: x.pins.__setitem__(123, h.n), "pin at position 123")
+    bad(lambda x: x.pins.__setitem__(int(h.eoff[short_e]) + 2, x.pins[int(h.eoff[short_e])]),
+        f"duplicate pin: a vertex appears twice in one edge (edge {short_e})")
+    bad(lambda x: x.pins.__setitem__(int(h.eoff[long_e + 1]) - 1, x.pins[int(h.eoff[long_e]) + 5]),
+        f"(edge {long_e})")
+
+    def empty_edge(x):
+        x.eoff[5] = x.eoff[4]  # edge 4 empty, edge 5 longer
+    bad(empty_edge, "eoff is not strictly increasing at edge 4")
+    o = oracle.match(h)
+    r = hmlib.solve_host(h)
+    assert np.array_equal(r.edges, o.edges) and r.rounds == o.rounds
+
+
 @pytest.mark.parametrize("n,m", [(50_000, 100_000), (400_000, 600_000)])
 def test_solve_host_rejects_bad_input(n, m):
     """A bad weight fails before the pins are used, a bad pin fails when they
