@@ -225,7 +225,8 @@ def method_argmax_bytes(stats: np.ndarray) -> float:
     active vertex 8 (entry 4, gathered priority-or-dead word 4). Units from
     hm_round_stats: the active vertices of round r (HM_STAT_NEXT) and the sum
     of their degrees (HM_STAT_DEG). The fixed order resumes each vertex at its
-    cursor instead, so the kernel moves fewer bytes than this count."""
+    cursor, and the re-randomised rounds scan compacted lists, so the kernels
+    move fewer bytes than this count."""
     NEXT, DEG = 7, 9
     s = stats.astype(np.float64)
     return float(s[:, NEXT].sum() * 24 + s[:, DEG].sum() * 8)
@@ -590,7 +591,7 @@ def run_ours(args, world, rank, local):
     # bytes where its step is the argmax of the fixed order, else this
     # design's counts; both are reported
     design_gbs = kb[dom] / (prof[dom][0] / 1e3) / 1e9
-    if dom == "argmax" and not rnd_mode:
+    if dom == "argmax" and stats[:, 9].sum() > 0:  # HM_STAT_DEG, filled by the replay
         alg_bytes, bytes_model = method_argmax_bytes(stats), (
             "method step a1: 24 B per active vertex + 8 B per list entry of an active vertex")
     else:

@@ -215,12 +215,11 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
 #define HM_STAT_NEXT      7  /* vertices kept for the next round */
 #define HM_STAT_LIVE      8  /* re-randomised rounds: live entries the argmax scan
                                 found; 0 in the fixed order */
-#define HM_STAT_DEG       9  /* fixed order, after hm_profile_match only (a counting
-                                kernel it runs between its timed kernels): sum of
-                                the degrees of the vertices kept (HM_STAT_NEXT: the
-                                unmatched vertices with a live edge at the start of
-                                the round); 0 after hm_match and in the
-                                re-randomised rounds */
+#define HM_STAT_DEG       9  /* after hm_profile_match only (a counting kernel it
+                                runs between its timed kernels): sum of the degrees
+                                of the vertices kept (HM_STAT_NEXT: the unmatched
+                                vertices with a live edge at the start of the
+                                round); 0 after hm_match */
 #define HM_STATS_COLS     10
 /* Returns the number of rows written in *rows_out. Errors: HM_EINVAL. */
 hm_status hm_round_stats(hm_handle *h, int64_t *stats, int32_t max_rounds, int32_t *rows_out);

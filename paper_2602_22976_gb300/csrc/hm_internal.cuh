@@ -96,7 +96,7 @@ struct DevState {
     unsigned long long proposals;
     unsigned long long lpack;      // re-randomised rounds: (long lists << 32) | their chunks
     unsigned long long live;       // re-randomised rounds: live entries found by the scan
-    unsigned long long sdeg;       // fixed order, profiled rounds: degrees of the vertices kept
+    unsigned long long sdeg;       // profiled rounds: degrees of the vertices kept
     unsigned long long kpack;      // kill ranges of the round: (entries << 32) | items
 };
 
@@ -309,6 +309,9 @@ void free_handle_buffers(Handle *h);
 // a.win (the re-randomised rounds): win kernel, then the kill kernel, which
 // also ends the round. The kill step reads the edge id of list entry p at
 // a.vadj[p * kill_stride]. ev (or null): events 1-4 of a profiled round.
+// Profiled rounds only: records ev[5] (the end of the argmax span), then
+// counts the degrees of the vertices the argmax step kept (HM_STAT_DEG).
+void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int random);
 void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev,
                          int kill_stride = 1);
 // Captures `capture(stream)` into g after the current nodes and returns the

@@ -487,6 +487,7 @@ void launch_rround(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEven
     k_rargmax<<<h->rargmax_grid, kT, 0, s>>>(a);
     k_rlong<<<h->rlong_grid, kT, 0, s>>>(a);
     k_rfin<<<(unsigned)h->sm_count, kT, 0, s>>>(a);
+    if (ev) launch_kept_degrees(h, a, s, ev, 1);
     launch_win_kill_end(h, a, s, ev, 2);
 }
 
@@ -604,7 +605,7 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "profile round");
         for (int k = 0; k < 4; ++k) {
-            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            cudaEventElapsedTime(&t, ev[k], k == 0 ? ev[5] : ev[k + 1]);
             ms[HM_K_ARGMAX + k] += t;
             // the argmax step is three kernels here; the round end is part of the kill kernel
             launches[HM_K_ARGMAX + k] += k == 0 ? 3 : (k == 3 ? 0 : 1);

@@ -426,18 +426,21 @@ def _active_sets(h, o):
 def test_active_vertices_and_their_degrees_per_round():
     """The argmax step's count of the vertices it keeps (HM_STAT_NEXT) and the
     replay's count of their degrees (HM_STAT_DEG) equal, round by round, the
-    active vertex sets of the oracle's run and their degree sums. A plain
-    match leaves the degree column at 0."""
+    active vertex sets of the oracle's run and their degree sums, in the
+    fixed order and in re-randomised rounds. A plain match leaves the degree
+    column at 0."""
     nxt = hmlib.STAT_COLUMNS.index("next")
     dg = hmlib.STAT_COLUMNS.index("deg")
     cases = [synth.large(seed=5, n=300_000, m=600_000), synth.small(seed=3),
              synth.unweighted(seed=2, n=100_000, m=200_000), synth.rgg(seed=4, n=50_000),
              synth.from_edges(7, [[0, 1], [1, 2], [2, 3], [3, 4]], None, seed=1)]
-    for h in cases:
-        o = oracle.match(h)
+    for h, noise in [(c, 0.0) for c in cases] + [(cases[0], 1.0), (cases[3], 0.5)]:
+        o = oracle.match(h, noise=noise)
         u, sdeg = _active_sets(h, o)
         assert sdeg[0] == h.kappa
         with hmlib.Matcher.from_hypergraph(h) as mt:
+            if noise:
+                mt.set_noise(noise)
             mt.match()
             res = mt.result()
             plain = mt.round_stats()
