@@ -597,6 +597,9 @@ def run_ours(args, world, rank, local):
     else:
         alg_bytes, bytes_model = kb[dom], "this design's per-unit counts (kernel_bytes)"
     achieved = alg_bytes / (prof[dom][0] / 1e3) / 1e9
+    # the DRAM bytes the kernel actually moved (ncu, committed summary) over the same time
+    traffic = measured_traffic(dom, rnd_mode, args.workload)
+    traffic_gbs = traffic * prof[dom][1] / (prof[dom][0] / 1e3) / 1e9 if traffic else None
     per_kernel = {k: {"ms": prof[k][0], "launches": prof[k][1], "alg_bytes": kb[k],
                       "gbs": (kb[k] / (prof[k][0] / 1e3) / 1e9) if prof[k][0] > 0 else None}
                   for k in hm.KERNELS}
@@ -705,7 +708,8 @@ def run_ours(args, world, rank, local):
                                     "p99": float(np.percentile(step_ms, 99))},
             "create_ms": create_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, rnd_mode, args.workload),
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_gbs": traffic_gbs,
+                         "traffic_frac": traffic_gbs / peaks["hbm_gbs"] if traffic_gbs else None,
                          "alg_bytes_per_launch": alg_bytes / max(1, prof[dom][1]), "bytes_model": bytes_model,
                          "design_bytes_per_launch": kb[dom] / max(1, prof[dom][1]),
                          "design_frac": design_gbs / peaks["hbm_gbs"],
