@@ -429,7 +429,8 @@ def run_batch(args, world, rank, local):
                    "class_launch_configs": cfg.tolist(), "l2": "inputs larger than L2",
                    "classes": "one union (HM_ONE_CLASS)" if args.one_class else "size classes by kappa (factors of 4)"},
         "instances_per_s": count * world * args.steps / (t_max / 1e3),
-        "time_to_matching_ms": {"median": statistics.median(step_ms)},
+        "time_to_matching_ms": {"median": statistics.median(step_ms), "mean": t_ms / len(step_ms),
+                                "p99": float(np.percentile(step_ms, 99))},
         "create_s": t_create, "generate_s": t_gen,
         "plain_per_instance": None if plain_ms is None else {
             "ms": plain_ms, "value": units_step / (plain_ms / 1e3), "unit": "pins/s",
