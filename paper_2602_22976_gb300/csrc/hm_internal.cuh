@@ -151,6 +151,8 @@ struct RoundArgs {
     uint64_t noise_s0;          // SplitMix64 start state of the priority stream
     const int2 *vadjE;          // vertex lists as {input edge id, bits(base priority)}
     int2 *vadjR;                // working copy, compacted every round
+    const int32_t *vnbrE;       // graphs: other endpoint of every vadjE entry
+    int32_t *vnbrR;             // graphs: the same for vadjR, compacted with it
     const int32_t *jof;         // input id -> j
     uint32_t *P2;               // second proposal counter buffer
     int2 *lq;                   // long lists of the round: {vertex, first chunk}
@@ -199,6 +201,8 @@ struct Handle {
     int4 *vrecR = nullptr;      // {T[v], 0, list start, live list length}
     int2 *vadjE = nullptr;      // vertex lists as {input edge id, bits(base priority)} (built once)
     int2 *vadjR = nullptr;      // working copy: short lists rewritten every match, long ones never
+    int32_t *vnbrE = nullptr;   // graphs: other endpoint of every list entry (liveness from vmatch)
+    int32_t *vnbrR = nullptr;   // graphs: working copy, compacted with vadjR
     int32_t *jof = nullptr;
     uint32_t *P2 = nullptr;
     int2 *lq = nullptr;

@@ -752,8 +752,8 @@ void (*argmax_kernel(const Handle *h))(RoundArgs) {
 }
 
 void launch_kill(const Handle *h, const RoundArgs &a, cudaStream_t s, int kill_stride) {
-    if (kill_stride == 2) k_kill<2><<<h->kill_grid, kT, 0, s>>>(a);
-    else if (a.pairs) k_kill<1><<<1, kT, 0, s>>>(a);  // nothing to kill: one block ends the round
+    if (a.pairs) k_kill<1><<<1, kT, 0, s>>>(a);  // graphs: nothing to kill, one block ends the round
+    else if (kill_stride == 2) k_kill<2><<<h->kill_grid, kT, 0, s>>>(a);
     else k_kill<1><<<h->kill_grid, kT, 0, s>>>(a);
 }
 
@@ -1132,7 +1132,7 @@ hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_m
 
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
     const int4 *vrec = h->last_random ? h->vrecR : h->vrec;
-    const uint8_t *vmatch = h->last_random ? nullptr : h->vmatch;  // set for graphs only
+    const uint8_t *vmatch = h->vmatch;  // graphs (both orders): the matched flags
     k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(vrec, vmatch, h->order, h->n,
                                                                                out_dev);
     return cudaGetLastError();

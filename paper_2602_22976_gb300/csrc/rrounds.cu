@@ -45,7 +45,11 @@
 // field stays 0, so the kill range of a matched vertex is its whole
 // (compacted) list, and the kill step (reading every second word: the edge
 // ids of the pairs; from vadjE in round 1) clears the flags of the input ids
-// there.
+// there. Graphs (every edge has two pins) need no kill: each list entry
+// also has its edge's other endpoint (vnbrE, compacted into vnbrR with the
+// pairs), an entry is live while that endpoint is unmatched, the win step
+// only sets the matched flags of the winners' endpoints, and a vertex whose
+// own flag is set drops out.
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
             a.inM[i] = 0;
         }
         if (i < a.n) {
+            if (a.pairs) a.vmatch[i] = 0;
             const int64_t b = a.voff[i], e = a.voff[i + 1];
             a.vrec[i] = make_int4(a.firstj[i], 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
         }
@@ -186,6 +191,7 @@ __device__ __noinline__ void flush_winners(const RoundArgs &a, uint64_t base, ui
 // regions are those of the fixed-order loop; warps of a persistent grid
 // take them one at a time from a counter, so that regions with long lists
 // do not leave other warps idle.
+template <bool kPairs>
 __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     DevState *st = a.st;
     const int r = st->round;
@@ -201,6 +207,8 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     // compact the working copy in place
     const int2 *src = r <= 2 ? a.vadjE : a.vadjR;
     int2 *dst = a.vadjR;
+    const int32_t *nsrc = r <= 2 ? a.vnbrE : a.vnbrR;  // graphs
+    int32_t *ndst = a.vnbrR;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     unsigned long long scanned = 0, props = 0, nlive = 0;
@@ -222,8 +230,9 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
             const uint32_t i = i0 + lane;
             const bool ok = i < count;
             const int32_t v = ok ? (r == 1 ? (int32_t)(base + i) : in[base + i]) : 0;
+            const bool mine = kPairs && ok && __ldg(a.vmatch + v) != 0;  // graphs: v is matched
             const int4 rec = ok ? a.vrec[v] : make_int4(kCurNone, 0, 0, 0);
-            const bool act = rec.x >= 0;
+            const bool act = rec.x >= 0 && !mine;
             const bool lng = act && (uint32_t)rec.w > kLong;
             if (lng) {  // queue slot and first chunk from one atomic, so both ascend together
                 const uint32_t nch = ((uint32_t)rec.w + kChunk - 1) / kChunk;
@@ -248,6 +257,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                 uint32_t opre[kU];
                 int64_t ob[kU];
                 int2 ev[kU];
+                int32_t nbv[kU];  // graphs: the other endpoint of each entry
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     // owner of position p: the largest lane x with pre_x <= p
@@ -268,12 +278,14 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                 for (int u = 0; u < kU; ++u) {
                     const uint32_t p = s0 + 32 * u + lane;
                     ev[u] = p < total ? src[ob[u] + (int64_t)(p - opre[u])] : make_int2(0, 0);
+                    if (kPairs) nbv[u] = p < total ? nsrc[ob[u] + (int64_t)(p - opre[u])] : 0;
                 }
                 bool lvv[kU];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const uint32_t p = s0 + 32 * u + lane;
-                    lvv[u] = p < total && (r == 1 || __ldg(a.alive + ev[u].x) != 0);
+                    lvv[u] = p < total &&
+                             (r == 1 || (kPairs ? __ldg(a.vmatch + nbv[u]) == 0 : __ldg(a.alive + ev[u].x) != 0));
                 }
                 __syncwarp();  // every read of this batch precedes its compaction writes
 #pragma unroll
@@ -288,7 +300,10 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                         const unsigned seg_lt = lt & ~((1u << sst) - 1u);
                         const unsigned lm = __ballot_sync(kFull, lv);
                         const uint32_t carried = __shfl_sync(kFull, live, o[u]);
-                        if (lv && r > 1) dst[ob[u] + carried + __popc(lm & seg_lt)] = ev[u];  // compaction
+                        if (lv && r > 1) {  // compaction
+                            dst[ob[u] + carried + __popc(lm & seg_lt)] = ev[u];
+                            if (kPairs) ndst[ob[u] + carried + __popc(lm & seg_lt)] = nbv[u];
+                        }
                         // segmented running maximum over the step
                         unsigned long long mx = key;
 #pragma unroll
@@ -348,6 +363,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
 
 // Chunks of the long lists: one warp per chunk of kChunk entries, maximum
 // key of the live entries combined per list with atomicMax.
+template <bool kPairs>
 __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
@@ -373,7 +389,7 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
             unsigned long long mx = 0;
             for (int64_t p = b + lane; p < e; p += 32) {
                 const int2 x = __ldg(a.vadjE + p);  // long lists are never compacted
-                if (r == 1 || __ldg(a.alive + x.x)) {
+                if (r == 1 || (kPairs ? __ldg(a.vmatch + __ldg(a.vnbrE + p)) == 0 : __ldg(a.alive + x.x) != 0)) {
                     const unsigned long long k = round_key(a, r, (uint32_t)x.x, __int_as_float(x.y));
                     if (k > mx) mx = k;
                     ++nlive;
@@ -432,6 +448,13 @@ __global__ void __launch_bounds__(kT) k_rfin(RoundArgs a) {
     block_add_u64(props, s_red, &st->proposals);
 }
 
+// Graphs: the other endpoint of every list entry (the second word of the
+// fixed order's {edge, endpoint} pairs, in the same list order).
+__global__ void __launch_bounds__(kT) k_pair_endpoints(const int2 *vpair, uint64_t kappa, int32_t *vnbrE) {
+    for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += (uint64_t)gridDim.x * kT)
+        vnbrE[i] = vpair[i].y;
+}
+
 // Lists as {input edge id, bits(base priority)} pairs, both copies, and
 // the inverse of the edge order (built once per handle).
 __global__ void __launch_bounds__(kT) k_map(const int32_t *order, const int32_t *vadj, const float *w, int64_t m,
@@ -460,7 +483,9 @@ int fit_per_sm(K kernel) {
 RoundArgs rand_args(const Handle *h) {
     RoundArgs a = round_args(h);
     a.vrec = h->vrecR;
-    a.pairs = 0;  // the re-randomised rounds keep their own lists and kill step
+    a.pairs = h->graph ? 1 : 0;  // graphs: liveness from vmatch, flag-only win, no kill
+    a.vnbrE = h->vnbrE;
+    a.vnbrR = h->vnbrR;
     a.vadj = reinterpret_cast<const int32_t *>(h->vadjR);  // for the kill step: stride 2
     a.vadjE = h->vadjE;
     a.vadjR = h->vadjR;
@@ -484,8 +509,13 @@ void launch_rinit(const Handle *h, const RoundArgs &a, cudaStream_t s) {
 
 void launch_rround(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
-    k_rargmax<<<h->rargmax_grid, kT, 0, s>>>(a);
-    k_rlong<<<h->rlong_grid, kT, 0, s>>>(a);
+    if (a.pairs) {
+        k_rargmax<true><<<h->rargmax_grid, kT, 0, s>>>(a);
+        k_rlong<true><<<h->rlong_grid, kT, 0, s>>>(a);
+    } else {
+        k_rargmax<false><<<h->rargmax_grid, kT, 0, s>>>(a);
+        k_rlong<false><<<h->rlong_grid, kT, 0, s>>>(a);
+    }
     k_rfin<<<(unsigned)h->sm_count, kT, 0, s>>>(a);
     if (ev) launch_kept_degrees(h, a, s, ev, 1);
     launch_win_kill_end(h, a, s, ev, 2);
@@ -532,8 +562,8 @@ hm_status build_graph_rand(Handle *h) {
 }  // namespace
 
 hm_status rand_prepare(Handle *h, cudaStream_t s) {
-    h->rargmax_grid = (unsigned)(h->sm_count * fit_per_sm(k_rargmax));
-    h->rlong_grid = (unsigned)(h->sm_count * fit_per_sm(k_rlong));
+    h->rargmax_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_rargmax<true>) : fit_per_sm(k_rargmax<false>)));
+    h->rlong_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_rlong<true>) : fit_per_sm(k_rlong<false>)));
     if (h->vrecR) return HM_OK;
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
     h->lq_cap = (uint32_t)(std::min<uint64_t>(n, h->kappa / kLong) + 1);
@@ -544,10 +574,14 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
         (st = dalloc(&h->jof, m, s, "inverse edge order")) != HM_OK ||
         (st = dalloc(&h->P2, m, s, "second proposal counters")) != HM_OK ||
         (st = dalloc(&h->lq, h->lq_cap, s, "long-list queue")) != HM_OK ||
-        (st = dalloc(&h->lbest, h->lq_cap, s, "long-list maxima")) != HM_OK) {
+        (st = dalloc(&h->lbest, h->lq_cap, s, "long-list maxima")) != HM_OK ||
+        (h->graph && ((st = dalloc(&h->vnbrE, h->kappa, s, "list endpoints")) != HM_OK ||
+                      (st = dalloc(&h->vnbrR, h->kappa, s, "re-randomised list endpoints")) != HM_OK))) {
         free_rand_buffers(h);
         return st;
     }
+    if (h->graph && h->kappa)  // the endpoints in list order, from the fixed order's pair lists
+        k_pair_endpoints<<<grid_for(h->kappa, kT, h->sm_count, 16), kT, 0, s>>>(h->vpair, h->kappa, h->vnbrE);
     if (m) {
         k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
             h->order, h->vadj, h->weighted ? h->weights : nullptr, h->m, h->kappa, h->vadjE, h->vadjR, h->jof);
@@ -618,7 +652,7 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
 }
 
 void free_rand_buffers(Handle *h) {
-    void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->lbest};
+    void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->lbest, h->vnbrE, h->vnbrR};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, h->cap_stream);
     h->vrecR = nullptr;
@@ -628,6 +662,8 @@ void free_rand_buffers(Handle *h) {
     h->P2 = nullptr;
     h->lq = nullptr;
     h->lbest = nullptr;
+    h->vnbrE = nullptr;
+    h->vnbrR = nullptr;
     if (h->exec_rand) cudaGraphExecDestroy(h->exec_rand);
     h->exec_rand = nullptr;
 }
