@@ -62,6 +62,7 @@ constexpr int kT = 256;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kLong = 2048;   // lists longer than this are scanned in chunks
 constexpr uint32_t kChunk = 2048;  // entries per chunk of a long list
+constexpr uint32_t kSeqMax = 64;   // graphs, round 1: tiles whose lists are all this short go one list per lane
 constexpr int kU = 4;              // 32-entry steps with loads in flight together
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -98,11 +99,30 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
 // key_r(e) of input edge e whose base priority is `base`. The product and
 // the sum are rounded separately (no fused multiply-add), as the
 // definition's float32 operations are.
-__device__ __forceinline__ unsigned long long round_key(const RoundArgs &a, int r, uint32_t e, float base) {
-    const uint64_t x = splitmix64_at(a.noise_s0, ((uint64_t)(uint32_t)r << 32) + e + 1u);
+__device__ __forceinline__ unsigned long long round_key_of(uint64_t s0, float scale, int r, uint32_t e, float base) {
+    const uint64_t x = splitmix64_at(s0, ((uint64_t)(uint32_t)r << 32) + e + 1u);
     const float u = __uint2float_rn((uint32_t)(x >> 40));
-    const float p = __fadd_rn(base, __fmul_rn(u, a.noise_scale));
+    const float p = __fadd_rn(base, __fmul_rn(u, scale));
     return ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(0xFFFFFFFFu - e);
+}
+
+__device__ __forceinline__ unsigned long long round_key(const RoundArgs &a, int r, uint32_t e, float base) {
+    return round_key_of(a.noise_s0, a.noise_scale, r, e, base);
+}
+
+// Round 1 of a graph, a tile whose lists are all short: each lane takes the
+// largest key of its own list, read from the immutable lists (every entry
+// is live in round 1, and nothing is written). Kept out of line so that the
+// tile path of k_rargmax keeps its own code.
+__device__ __noinline__ unsigned long long first_round_max(const int2 *vadjE, int64_t lb, uint32_t len, uint64_t s0,
+                                                           float scale) {
+    unsigned long long best = 0;
+    for (uint32_t i = 0; i < len; ++i) {
+        const int2 ev = __ldg(vadjE + lb + i);
+        const unsigned long long key = round_key_of(s0, scale, 1, (uint32_t)ev.x, __int_as_float(ev.y));
+        if (key > best) best = key;
+    }
+    return best;
 }
 
 __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
@@ -247,11 +267,22 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
             }
             // the short and medium lists of the tile as one sequence
             const uint32_t L = act && !lng ? (uint32_t)rec.w : 0u;
+            unsigned long long best = 0;
+            uint32_t live = 0;
+            uint32_t Lmax = 0;
+            if (kPairs && r == 1) {
+                Lmax = L;
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) Lmax = max(Lmax, __shfl_xor_sync(kFull, Lmax, d));
+            }
+            if (kPairs && r == 1 && Lmax <= kSeqMax) {  // warp-uniform
+                if (L) best = first_round_max(a.vadjE, (int64_t)(uint32_t)rec.z, L, a.noise_s0, a.noise_scale);
+                live = L;
+                scanned += L;
+            } else {
             const uint32_t inc = warp_inclusive_scan(L);
             const uint32_t pre = inc - L;
             const uint32_t total = __shfl_sync(kFull, inc, 31);
-            unsigned long long best = 0;
-            uint32_t live = 0;
             for (uint32_t s0 = 0; s0 < total; s0 += 32 * kU) {
                 int o[kU];
                 uint32_t opre[kU];
@@ -324,6 +355,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                         scanned += su + lane < total ? 1u : 0u;
                     }
                 }
+            }
             }
             bool keep = false, w = false;
             int32_t nb = -1;
