@@ -15,6 +15,7 @@ import torch
 
 import oracle
 import synth
+from cursor_work import active_sets as _active_sets, entries_ahead_of_the_match as _entries_ahead_of_the_match
 import paper_2602_22976_gb300 as hmlib
 from conftest import golden_cases, golden_hypergraph
 
@@ -379,20 +380,6 @@ def test_each_list_entry_touched_once():
         assert int(stats[:, adv].sum() + stats[:, kills].sum()) == h.kappa
 
 
-def _entries_ahead_of_the_match(h, o):
-    """Over a whole run, the cursor of a vertex passes exactly the entries of
-    its list that rank above its matching edge, or its whole list if it stays
-    unmatched: summed over the vertices, from the oracle's matching."""
-    keys = oracle.keys(h)
-    eid = np.repeat(np.arange(h.m), np.diff(h.eoff))
-    mv = np.full(h.n, -1, dtype=np.int64)
-    won = o.in_matching[eid] == 1
-    mv[h.pins[won]] = eid[won]
-    matched = mv >= 0
-    ahead = matched[h.pins] & (keys[eid] > keys[np.maximum(mv[h.pins], 0)])
-    return int(ahead.sum()) + int(np.bincount(h.pins, minlength=h.n)[~matched].sum())
-
-
 def test_graph_cursors_pass_each_entry_once():
     """Graphs run without a kill step (an edge is live while neither endpoint
     is matched): the kill counter stays 0, and the entries the cursors skip
@@ -408,19 +395,6 @@ def test_graph_cursors_pass_each_entry_once():
         assert res.status == OK and np.array_equal(res.edges, o.edges) and res.rounds == o.rounds
         assert not stats[:, kills].any()
         assert int(stats[:, adv].sum()) == _entries_ahead_of_the_match(h, o)
-
-
-def _active_sets(h, o):
-    """From the oracle's run: for every round r, the vertices active at its
-    start (unmatched, with a live edge: some incident edge is decided in round
-    r or later) and the sum of their degrees."""
-    sizes = np.diff(h.eoff)
-    dec = o.decided_round.astype(np.int64)
-    vmax = np.zeros(h.n, dtype=np.int64)
-    np.maximum.at(vmax, h.pins, np.repeat(dec, sizes))
-    deg = np.bincount(h.pins, minlength=h.n)
-    return ([int((vmax >= r).sum()) for r in range(1, o.rounds + 1)],
-            [int(deg[vmax >= r].sum()) for r in range(1, o.rounds + 1)])
 
 
 def test_active_vertices_and_their_degrees_per_round():

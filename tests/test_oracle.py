@@ -370,3 +370,72 @@ def test_weight_is_the_exact_sum_rounded_once():
         mask = rng.random(m) < 0.6
         exact = sum((Fraction(float(x)) for x in w[mask]), Fraction(0))
         assert oracle.weight(types.SimpleNamespace(weights=w), mask.astype(np.uint8)) == float(exact)
+
+
+def _replay_rounds(h):
+    """The fixed-order rounds replayed directly on tiny inputs (plain Python,
+    independent of the oracle's C code): each vertex keeps a cursor into its
+    list sorted by decreasing key; at the start of a round every unmatched
+    vertex moves its cursor past dead entries (to the end when none is
+    left). Returns the active vertices per round, their degree sums, the
+    cursor moves over the run, the matching and the round count."""
+    keys = [int(k) for k in oracle.keys(h)]
+    edges = [h.pins[h.eoff[e]:h.eoff[e + 1]].tolist() for e in range(h.m)]
+    lists = [[] for _ in range(h.n)]
+    for e, pins in enumerate(edges):
+        for v in pins:
+            lists[v].append(e)
+    for v in range(h.n):
+        lists[v].sort(key=lambda e: -keys[e])
+    alive = [True] * h.m
+    matched = [False] * h.n
+    cur = [0] * h.n
+    moves, U, D, M, rounds = 0, [], [], [], 0
+    while True:
+        for v in range(h.n):
+            if not matched[v]:
+                c = cur[v]
+                while c < len(lists[v]) and not alive[lists[v][c]]:
+                    c += 1
+                moves += c - cur[v]
+                cur[v] = c
+        active = [v for v in range(h.n) if not matched[v] and cur[v] < len(lists[v])]
+        if not active:
+            break
+        rounds += 1
+        U.append(len(active))
+        D.append(sum(len(lists[v]) for v in active))
+        T = {v: lists[v][cur[v]] for v in active}
+        winners = [e for e in range(h.m) if alive[e] and all(T.get(v) == e for v in edges[e])]
+        for e in winners:
+            M.append(e)
+            for v in edges[e]:
+                matched[v] = True
+        for e in range(h.m):
+            if alive[e] and any(matched[v] for v in edges[e]):
+                alive[e] = False
+    return U, D, moves, sorted(M), rounds
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_active_sets_and_cursor_moves_by_replay(seed):
+    """The counts the GPU tests derive from the oracle's run - the active
+    vertices and their degree sums per round, and the entries the cursors
+    pass (those ahead of each vertex's matching edge, or its whole list) -
+    equal a direct replay of the rounds, whose matching and round count
+    equal the oracle's, on tiny hypergraphs and graphs with tied weights."""
+    from cursor_work import active_sets, entries_ahead_of_the_match
+    rng = np.random.default_rng(500 + seed)
+    for c in range(30):
+        n = int(rng.integers(2, 20))
+        m = int(rng.integers(1, 30))
+        graph = rng.random() < 0.4
+        edges = [rng.choice(n, size=2 if graph else int(rng.integers(1, min(n, 5) + 1)),
+                            replace=False).tolist() for _ in range(m)]
+        w = None if c % 4 == 3 else list(rng.choice([0.25, 0.5, 1.0], size=m))
+        h = synth.from_edges(n, edges, w, seed=seed + 1)
+        o = oracle.match(h)
+        U, D, moves, M, rounds = _replay_rounds(h)
+        assert M == o.edges.tolist() and rounds == o.rounds
+        assert (U, D) == active_sets(h, o)
+        assert moves == entries_ahead_of_the_match(h, o)
