@@ -19,6 +19,10 @@
 // touch a marked vertex are deactivated. The order on edges is the same
 // strict order as hm_match's, so the result is the same matching and round
 // count.
+//
+// hm_solve_host runs the same kernel for small inputs (solve_small below),
+// on working memory from the stream's pool, after k_check_small has checked
+// the input the way hm_create does.
 #include "hm_internal.cuh"
 #include "exact_sum.cuh"
 
