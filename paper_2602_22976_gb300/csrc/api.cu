@@ -12,17 +12,26 @@
 
 namespace hm {
 
-namespace {
-thread_local std::string g_err;
-
-bool device_pointer(const void *p) {
+bool usable_device_pointer(const void *p) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
 }
+
+namespace {
+thread_local std::string g_err;
+
+bool device_pointer(const void *p) { return usable_device_pointer(p); }
 
 hm_status einval(const char *msg) {
     g_err = msg;

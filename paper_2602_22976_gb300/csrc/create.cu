@@ -81,16 +81,6 @@ __global__ void k_validate(const int64_t *__restrict__ eoff, const int32_t *__re
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(&err->max_size, mx);
 }
 
-// MurmurHash3 32-bit finaliser (Appleby): a bijection on 32-bit words.
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    h *= 0xC2B2AE35u;
-    h ^= h >> 16;
-    return h;
-}
-
 // Sort key = complemented priority (ascending sort = decreasing priority).
 // Positive finite floats order like their bit patterns. For a union of
 // independent instances (inst_ebase != nullptr: first edge of each of the

@@ -98,6 +98,8 @@ struct DevState {
     unsigned long long live;       // re-randomised rounds: live entries found by the scan
     unsigned long long sdeg;       // profiled rounds: degrees of the vertices kept
     unsigned long long kpack;      // kill ranges of the round: (entries << 32) | items
+    unsigned long long ledges;     // profiled rounds: edges live at the start of the round
+    unsigned long long lpins;      // profiled rounds: their pins
 };
 
 // One kill range: list entries [begin, begin + length) where length is the
@@ -316,6 +318,9 @@ void free_handle_buffers(Handle *h);
 // Profiled rounds only: records ev[5] (the end of the argmax span), then
 // counts the degrees of the vertices the argmax step kept (HM_STAT_DEG).
 void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int random);
+// Profiled rounds only, before the round's timed kernels: counts the edges
+// live at the start of the round and their pins (HM_STAT_LEDGES/LPINS).
+void launch_live_edges(const Handle *h, const RoundArgs &a, cudaStream_t s, int random);
 void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev,
                          int kill_stride = 1);
 // Captures `capture(stream)` into g after the current nodes and returns the
@@ -344,6 +349,23 @@ __host__ __device__ inline uint64_t splitmix64_at(uint64_t s0, uint64_t k) {
     return x ^ (x >> 31);
 }
 __host__ __device__ inline uint64_t splitmix64_first(uint64_t seed) { return splitmix64_at(seed, 1); }
+
+// MurmurHash3 32-bit finaliser (Appleby): a bijection on 32-bit words. The
+// unweighted priority of edge e is fmix32(e ^ s), s = low 32 bits of
+// splitmix64_first(seed); every path that orders edges uses this one copy.
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// True when p is device memory usable by kernels of the current device:
+// memory of the current device, or managed memory. Memory of another GPU
+// is refused (without peer access a kernel would fault on it).
+bool usable_device_pointer(const void *p);
 
 // Stream-ordered device allocation of `count` elements (at least one);
 // HM_ENOMEM with a message naming `what` on failure.

@@ -2,11 +2,9 @@
 // one kernel launch, without allocating any memory.
 //
 // Who needs this: code that is not allowed to allocate device memory at the
-// moment it wants a matching. Examples are a caller in the middle of
-// capturing a CUDA graph on its stream (cudaMalloc is not a capturable call
-// and invalidates the capture), a host framework that owns every byte of
-// device memory through its own arena and forbids other allocators, and
-// latency-bound loops that cannot pay for cudaMalloc's implicit
+// moment it wants a matching. Examples are a host framework that owns every
+// byte of device memory through its own arena and forbids other allocators,
+// and latency-bound loops that cannot pay for cudaMalloc's implicit
 // synchronisation and page mapping. Such callers pass their inputs and
 // outputs; everything else this entry point needs lives in a fixed,
 // file-scope device array that the library declares once.
@@ -54,27 +52,12 @@ inline size_t scratch_bytes(int64_t n, int64_t m) {
     return align256((size_t)n * 8) + align256((size_t)n) + align256((size_t)m);
 }
 
-__device__ __forceinline__ uint32_t na_fmix32(uint32_t h) {
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    h *= 0xC2B2AE35u;
-    h ^= h >> 16;
-    return h;
-}
-
-__host__ __device__ inline uint64_t na_splitmix64_first(uint64_t x) {
-    x += 0x9E3779B97F4A7C15ULL;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
-    return x ^ (x >> 31);
-}
-
 // Packed key: larger wins. Weighted: weight bits, then smaller id first.
-// Unweighted: bits of 1.0f, then the seeded fmix32 priority.
+// Unweighted: bits of 1.0f, then the seeded fmix32 priority (the helpers
+// hm_create's order uses, so both paths order edges identically).
 __device__ __forceinline__ unsigned long long na_key(const float *w, uint32_t salt, int64_t e) {
     if (w) return ((unsigned long long)__float_as_uint(w[e]) << 32) | (0xFFFFFFFFull - (uint32_t)e);
-    return (0x3F800000ull << 32) | na_fmix32((uint32_t)e ^ salt);
+    return (0x3F800000ull << 32) | fmix32((uint32_t)e ^ salt);
 }
 
 constexpr int kNaThreads = 1024;
@@ -255,14 +238,9 @@ k_match_noalloc(const int64_t *__restrict__ eoff, const int32_t *__restrict__ pi
     }
 }
 
-bool on_device(const void *p) {
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+// Memory of the current device (or managed memory): the kernel is launched
+// on the current device, and memory of another GPU would fault there.
+bool on_device(const void *p) { return usable_device_pointer(p); }
 
 }  // namespace
 
@@ -311,7 +289,7 @@ hm_status solve_small(int64_t n, int64_t m, uint64_t kappa, const int64_t *eoff,
     if (e == cudaSuccess && weighted && m)
         e = cudaMemcpyAsync(d_w, weights, (size_t)m * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "hm_solve_host: upload");
-    const uint32_t salt = (uint32_t)na_splitmix64_first(seed);
+    const uint32_t salt = (uint32_t)splitmix64_first(seed);
     unsigned long long *d_first = reinterpret_cast<unsigned long long *>(buf + a_first);
     e = cudaMemsetAsync(d_first, 0xFF, 4 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "hm_solve_host: check state");
@@ -391,7 +369,7 @@ extern "C" hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff,
     }
     if (!on_device(eoff) || !on_device(result) || (m > 0 && (!on_device(pins) || !on_device(in_matching))) ||
         (m > 0 && weighted && !on_device(weights))) {
-        set_error("hm_match_noalloc: inputs and outputs must be device memory");
+        set_error("hm_match_noalloc: inputs and outputs must be device memory of the current device");
         return HM_EINVAL;
     }
     int dev = -1;
@@ -414,7 +392,10 @@ extern "C" hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff,
         }
         scratch = g_scratch_addr[dev];
     }
-    const uint32_t salt = (uint32_t)na_splitmix64_first(seed);
+    const uint32_t salt = (uint32_t)splitmix64_first(seed);
+    // a launch error is read back below: clear one that an earlier call of
+    // the caller left behind, so it is not reported as this launch's
+    cudaGetLastError();
     k_match_noalloc<<<1, kNaThreads, 0, (cudaStream_t)cuda_stream>>>(
         eoff, pins, weighted ? weights : nullptr, salt, n, m, in_matching, result,
         static_cast<unsigned char *>(scratch), nullptr);
