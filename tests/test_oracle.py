@@ -283,6 +283,31 @@ def test_splitmix64_stream_published_vectors():
     assert oracle.splitmix64_at(0, 3) == 0x06C45D188009454F
 
 
+@pytest.mark.parametrize("r,e,x,top24,bits", [
+    (1, 0, 0x1F69EA35BA1A6227, 2058730, 1059023338),
+    (2, 5, 0x18DD9D9FE048EE4E, 1629597, 1058594205),
+    (3, 7, 0xA8A8458085A42786, 11053125, 1066685474),
+])
+def test_round_priority_worked_example(r, e, x, top24, bits):
+    """p_r(e) for seed 0, weight 0.5, amplitude 1, worked step by step. The
+    priority stream starts at s0 = the first SplitMix64 output of seed 0,
+    0xE220A8397B1DCDAF (the published vector above); round r of edge e uses
+    output number k = (r << 32) + e + 1 of that stream, x; U = top 24 bits
+    of x times 2^-24; p = 0.5 + 1 * U, each operation rounded to float32
+    (the sum is the only inexact step here). A counter off by one in r or e
+    gives another x and fails this."""
+    s0 = 0xE220A8397B1DCDAF
+    assert oracle.splitmix64_first(0) == s0
+    k = (r << 32) + e + 1
+    assert oracle.splitmix64_at(s0, k) == x
+    assert x >> 40 == top24
+    u = np.float32(top24) * np.float32(2.0 ** -24)  # exact: a 24-bit integer times a power of two
+    p = np.float32(np.float32(0.5) + u)
+    assert int(p.view(np.uint32)) == bits
+    h = synth.from_edges(20, [[i, i + 1] for i in range(9)], [0.5] * 9, seed=0)
+    assert np.float32(oracle.round_priority(h, 1.0, r, e)) == p
+
+
 def test_round_priorities_in_range():
     h = synth.small(seed=2, n=1000, m=3000)
     ps = np.array([[oracle.round_priority(h, 100.0, r, e) - float(h.weights[e]) for e in range(0, 3000, 7)]
