@@ -67,13 +67,18 @@ L2_FLUSH_BYTES = 512 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 400 matches; 20 batch launches; 10 oracle runs for --impl reference)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="large")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: leave out the batch sub-object (the batching workload at full size)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="default workload: leave out the serve sub-object (short serving runs)")
     ap.add_argument("--no-plain", action="store_true",
                     help="batch workload: skip the one-hm_match-per-instance comparison")
     ap.add_argument("--one-class", action="store_true",
@@ -83,7 +88,10 @@ def parse():
     ap.add_argument("--noise", type=float, default=0.0,
                     help="> 0: the paper's re-randomised rounds with this noise amplitude "
                          "(priorities drawn again before every round); 0: fixed order")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else (20 if args.workload == "batch" else 400)
+    return args
 
 
 # ------------------------------------------------------------------ helpers
@@ -232,10 +240,35 @@ def method_argmax_bytes(stats: np.ndarray) -> float:
     return float(s[:, NEXT].sum() * 24 + s[:, DEG].sum() * 8)
 
 
+def method_match_bytes(stats: np.ndarray) -> dict:
+    """Bytes of the method's steps a1-a4 summed over rounds, by the per-unit
+    figures of the plain formulation (every active vertex takes the maximum
+    over its whole list, every live edge tests all its pins, every live edge
+    is checked against the matched flags, both lists are compacted):
+      a1  24 B per active vertex U_r + 8 B per list entry of an active vertex
+      a2  24 B per live edge A_r (list slot 4, offset pair 16, priority 4)
+          + 8 B per live pin pi_r (pin 4, gathered best 4)
+          + 1 B per pin of a winner (matched flag) + 1 B per winner (mask)
+      a3  5 B per live pin (pin 4, gathered matched flag 1) + 4 B per live
+          edge (priority-or-dead write)
+      a4  8 B per live edge and per active vertex (list read 4, write 4)
+    Units from hm_round_stats: U_r = HM_STAT_NEXT, sum of their degrees =
+    HM_STAT_DEG, A_r = HM_STAT_LEDGES, pi_r = HM_STAT_LPINS (the last three
+    filled by the per-kernel replay), winners and their pins."""
+    WIN, WPIN, NEXT, DEG, LED, LPI = 3, 4, 7, 9, 10, 11
+    s = stats.astype(np.float64)
+    a1 = s[:, NEXT].sum() * 24 + s[:, DEG].sum() * 8
+    a2 = s[:, LED].sum() * 24 + s[:, LPI].sum() * 8 + s[:, WPIN].sum() + s[:, WIN].sum()
+    a3 = s[:, LPI].sum() * 5 + s[:, LED].sum() * 4
+    a4 = (s[:, LED].sum() + s[:, NEXT].sum()) * 8
+    return {"a1": float(a1), "a2": float(a2), "a3": float(a3), "a4": float(a4),
+            "total": float(a1 + a2 + a3 + a4)}
+
+
 def random_access_roofline(stats: np.ndarray, prof: dict, ra: dict, random: bool) -> dict | None:
     """The round kernels are bound by random single-element accesses, not by
     bytes: a lower bound on each kernel's time is its random accesses at this
-    GPU's measured rates (hm_probe_random_access: 1-byte loads, 1-byte
+    GPU's measured rates (probe_random_access: 1-byte loads, 1-byte
     stores, returning 4-byte atomics). frac = that bound / the kernel's time.
     Counted from hm_round_stats, fixed order only: k_argmax does one live-flag
     load per active vertex and per skipped entry from round 2 on and one
@@ -261,15 +294,18 @@ def random_access_roofline(stats: np.ndarray, prof: dict, ra: dict, random: bool
     return out
 
 
-# kernel step of the bench line -> (row name in profiles/traffic.md, its source file)
+# kernel step of the bench line -> (kernel name in profiles/traffic.json, its source file)
 TRAFFIC_ROWS = {
+    ("init", False): ("k_init", "rounds.cu"),
     ("argmax", False): ("k_argmax", "rounds.cu"),
     ("win", False): ("k_win", "rounds.cu"),
     ("kill", False): ("k_kill", "rounds.cu"),
+    ("init", True): ("k_rinit", "rrounds.cu"),
     ("argmax", True): ("k_rargmax+k_rlong+k_rfin", "rrounds.cu"),
     ("win", True): ("k_win", "rounds.cu"),
     ("kill", True): ("k_kill", "rounds.cu"),
 }
+TRAFFIC_FILE = os.path.join("profiles", "traffic.json")
 
 
 def kernel_source_hash(source: str = "rounds.cu") -> str:
@@ -281,25 +317,64 @@ def kernel_source_hash(source: str = "rounds.cu") -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(step: str, randomised: bool, workload: str = "large") -> float | None:
-    """Per-launch DRAM bytes of a kernel step at the full bench size, read from
-    the committed ncu summary (profiles/traffic.md) when the row was measured
-    on this source, in this mode (fixed order / re-randomised rounds) and on
-    this workload (the power-law instance unless the mode names another)."""
-    p = os.path.join(ROOT, "profiles", "traffic.md")
-    row, source = TRAFFIC_ROWS[(step, randomised)]
-    if not os.path.exists(p):
+def traffic_row(step: str, randomised: bool, workload: str = "large") -> dict | None:
+    """The committed ncu row (profiles/traffic.json) of a kernel step, when it
+    was measured on this source, in this mode (fixed order / re-randomised
+    rounds) and on this workload; else None."""
+    p = os.path.join(ROOT, TRAFFIC_FILE)
+    if (step, randomised) not in TRAFFIC_ROWS or not os.path.exists(p):
         return None
+    name, source = TRAFFIC_ROWS[(step, randomised)]
     want = kernel_source_hash(source)
-    mode = ("re-randomised" if randomised else "fixed") + ("" if workload == "large" else f", {workload}")
-    for line in open(p):
-        parts = [x.strip() for x in line.strip().strip("|").split("|")]
-        if len(parts) >= 4 and parts[0] == row and parts[1] == mode and parts[2] == want:
-            try:
-                return float(parts[3])
-            except ValueError:
-                return None
-    return None
+    mode = "re-randomised" if randomised else "fixed"
+    with open(p) as f:
+        rows = json.load(f)["rows"]
+    best = None
+    for r in rows:
+        if r["kernel"] == name and r["mode"] == mode and r["workload"] == workload and r["source_hash"] == want:
+            if best is None or r.get("scale", 1) < best.get("scale", 1):  # a full-size capture first
+                best = r
+    return best
+
+
+def measured_traffic(step: str, randomised: bool, workload: str = "large",
+                     design_per_launch: float | None = None) -> float | None:
+    """DRAM bytes per launch of a kernel step at the bench's size, from the
+    committed ncu row. A row captured on a smaller instance (scale s > 1:
+    n and m divided by s) is scaled to the bench's size by the units the
+    kernel processes: its measured bytes times the ratio of this design's
+    element bytes per launch at the bench's size (design_per_launch) to those
+    of the captured run (the row's design_bytes_per_launch). Without that
+    ratio a scaled row reads as None."""
+    r = traffic_row(step, randomised, workload)
+    if r is None:
+        return None
+    b = float(r["bytes_per_launch"])
+    if r.get("scale", 1) == 1:
+        return b
+    if not design_per_launch or not r.get("design_bytes_per_launch"):
+        return None
+    return b * design_per_launch / float(r["design_bytes_per_launch"])
+
+
+PROBES = ("store1B", "load1B", "load4B", "red4B", "atomic4B")
+
+
+def probe_random_access(array_bytes: int, ops: int = 200_000_000, stream_handle: int | None = None) -> dict:
+    """Random single-element access rates of this GPU (1e9 per second), from
+    the benchmark's own probe library (libhmprobe.so, built beside libhm.so
+    but not part of it)."""
+    import ctypes
+    import importlib
+    L = ctypes.CDLL(importlib.import_module("paper_2602_22976_gb300.build").build_probe())
+    L.hmprobe_random_access.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    L.hmprobe_random_access.restype = ctypes.c_int
+    L.hmprobe_last_error.restype = ctypes.c_char_p
+    out = np.zeros(len(PROBES), dtype=np.float64)
+    rc = L.hmprobe_random_access(int(array_bytes), int(ops), out.ctypes.data, stream_handle)
+    if rc != 0:
+        raise RuntimeError(f"random-access probe failed ({rc}): {L.hmprobe_last_error().decode()}")
+    return dict(zip(PROBES, out.tolist()))
 
 
 def measured_peaks() -> dict:
@@ -315,14 +390,50 @@ def cpu_cores_used() -> int:
     return 1
 
 
+def host_cpu() -> dict:
+    """The host the CPU baselines run on: its core count and CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+# The paper's own headline (other hardware, its real-world instances and its
+# re-randomised rounds): printed beside the numbers as context only.
+PAPER_CONTEXT = {
+    "claim": "up to 76.6x speedup of the CUDA implementation (HLM:C) over single-core sequential Greedy",
+    "range": "3.20x to 76.6x across the paper's hypergraph categories",
+    "hardware": "NVIDIA RTX 4090 (GPU) vs one core of an Intel Xeon w5-3435X",
+    "where": "Sec. 5.2",
+    "note": "other hardware, other instances and per-round random weights: context, not a target",
+}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, world, rank):
+    """The CPU oracle (this project's reference) on the machine's host cores, on
+    the bench's own instance (the full workload where it has one; the batch
+    and serve workloads use a sample of their generator), one oracle run per
+    step. Under torchrun only rank 0 runs it."""
     if rank != 0:
         return
     import oracle
     wl = WORKLOADS[args.workload]
-    hs = wl["sample"](args.seed)
+    full = wl["make"] is not None
+    hs = wl["make"](args.seed, args.scale) if full else wl["sample"](args.seed)
     hs = hs if isinstance(hs, list) else [hs]
     oracle.build()
     for _ in range(args.warmup):
@@ -333,30 +444,111 @@ def run_reference(args, world, rank):
     for _ in range(args.steps):
         units = sum(h.kappa * oracle.match(h, noise=args.noise).rounds for h in hs)
     dt = time.perf_counter() - t0
-    value = units * args.steps / dt
-    sample = (f"{hs[0].name}: kappa={hs[0].kappa}, one oracle run per step" if len(hs) == 1 else
-              f"{len(hs)} instances of the batch generator, kappa={sum(h.kappa for h in hs)}, "
-              f"one oracle run of each per step")
+    value = units * args.steps / dt if dt > 0 else 0.0
+    if full:
+        sample = (f"the bench's own instance{f' scaled 1/{args.scale}' if args.scale > 1 else ''} "
+                  f"(kappa={hs[0].kappa}), one oracle run per step")
+    else:
+        sample = (f"{len(hs)} instances of the {args.workload} generator, kappa={sum(h.kappa for h in hs)}, "
+                  f"one oracle run of each per step")
+    desc = wl["desc"] + (f" scaled 1/{args.scale}" if full and args.scale > 1 else "")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample,
-                                        "noise": args.noise},
+        "data": "synthetic", "config": {"workload": desc, "sample": sample, "noise": args.noise,
+                                        "same_instance_as_gpu_arm": full},
         "cpu_baseline": {"value": value, "unit": "pins/s", "cores": cpu_cores_used(),
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample, "host": host_cpu()},
         "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "paper_context": PAPER_CONTEXT,
     }
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ batched arm
 
+def measure_batch(seed: int, count: int, steps: int, warmup: int, one_class: bool = False,
+                  plain: bool = True, stream=None) -> dict:
+    """The batching workload: `count` independent instances in one
+    hm_batch_match (one graph launch, autotuned size classes), timed with
+    CUDA events over `steps` launches; then the same instances as one handle
+    and one hm_match each (the plain per-instance launch), all launched back
+    to back on the same stream and timed the same way. Results of the two
+    paths are compared instance by instance."""
+    import torch
+    import synth
+    import paper_2602_22976_gb300 as hm
+    stream = stream or torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    hs = synth.batch(count, seed=seed)
+    for h in hs:
+        h.seed = 1
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = hm.Batch(hs, autotune=True, one_class=one_class)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    for _ in range(max(warmup, 3)):
+        b.match(stream)
+    res = b.result()
+    units_step = float(sum(h.kappa * r.rounds for h, r in zip(hs, res)))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        starts[k].record(stream)
+        b.match(stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [x.elapsed_time(y) for x, y in zip(starts, ends)]
+    t_ms = float(sum(step_ms))
+    ncls, cls, cfg = b.info()
+    b.close()
+    plain_out = None
+    if plain:
+        t0 = time.perf_counter()
+        mts = [hm.Matcher.from_hypergraph(h) for h in hs]
+        t_plain_create = time.perf_counter() - t0
+        for mt in mts:
+            mt.match(stream)
+        torch.cuda.synchronize()
+        reps = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for mt in mts:
+                mt.match(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            reps.append(e0.elapsed_time(e1))
+        same = True
+        for mt, r in zip(mts, res):
+            rr = mt.result()
+            same = same and rr.rounds == r.rounds and np.array_equal(rr.edges, r.edges)
+            mt.close()
+        plain_ms = statistics.median(reps)
+        plain_out = {"ms": plain_ms, "ms_runs": reps, "value": units_step / (plain_ms / 1e3), "unit": "pins/s",
+                     "launches": f"{count} hm_match graph launches back to back on one stream",
+                     "create_s": t_plain_create, "same_results_as_batch": bool(same),
+                     "batched_speedup": plain_ms / (t_ms / steps)}
+    return {
+        "value": units_step * steps / (t_ms / 1e3), "unit": "pins/s", "steps": steps,
+        "ms_per_launch": t_ms / steps,
+        "time_to_matching_ms": {"median": statistics.median(step_ms), "mean": t_ms / steps,
+                                "p99": float(np.percentile(step_ms, 99))},
+        "instances": count, "instances_per_s": count * steps / (t_ms / 1e3),
+        "sum_kappa": int(sum(h.kappa for h in hs)), "sum_n": int(sum(h.n for h in hs)),
+        "units_per_launch": units_step, "size_classes": int(ncls), "class_launch_configs": cfg.tolist(),
+        "classes": "one union (HM_ONE_CLASS)" if one_class else "size classes by kappa (factors of 4)",
+        "create_s": t_create, "generate_s": t_gen, "plain_per_instance": plain_out,
+    }
+
+
 def run_batch(args, world, rank, local):
     """One step = one hm_batch_match over all instances (one graph launch);
     compared with one hm_match per instance on the same GPU."""
     import torch
-    import synth
     import paper_2602_22976_gb300 as hm
 
     import torch.distributed as dist
@@ -365,77 +557,22 @@ def run_batch(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hm.build()
     count = max(1, 4096 // args.scale)
-    t0 = time.perf_counter()
-    hs = synth.batch(count, seed=replica_seed(args.seed, rank))
-    for h in hs:
-        h.seed = args.seed
-    t_gen = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    b = hm.Batch(hs, autotune=True, one_class=args.one_class)
-    torch.cuda.synchronize()
-    t_create = time.perf_counter() - t0
-    stream = torch.cuda.current_stream()
-    for _ in range(max(args.warmup, 3)):
-        b.match(stream)
-    res = b.result()
-    units_step = float(sum(h.kappa * r.rounds for h, r in zip(hs, res)))
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(local)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    time.sleep(0.3)
-    for k in range(args.steps):
-        starts[k].record(stream)
-        b.match(stream)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    r = measure_batch(replica_seed(args.seed, rank), count, args.steps, args.warmup, args.one_class,
+                      plain=not args.no_plain)
     clk = clocks.stop()
-    step_ms = [x.elapsed_time(y) for x, y in zip(starts, ends)]
-    t_ms = float(sum(step_ms))
-    units_all, t_max = replica_totals(units_step * args.steps, t_ms, world)
-    ncls, cls, cfg = b.info()
-    b.close()
-    # plain per-instance launches: one handle and one hm_match per instance
-    plain_ms = None
-    if not args.no_plain:
-        mts = [hm.Matcher.from_hypergraph(h) for h in hs]
-        for mt in mts:
-            mt.match(stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for mt in mts:
-            mt.match(stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        plain_ms = e0.elapsed_time(e1)
-        for mt, r in zip(mts, res):
-            rr = mt.result()
-            assert rr.rounds == r.rounds and rr.count == r.count
-            mt.close()
+    units_all, t_max = replica_totals(r["units_per_launch"] * args.steps, r["ms_per_launch"] * args.steps, world)
     out = {
         "metric": METRIC, "value": units_all / (t_max / 1e3), "unit": "pins/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS["batch"]["desc"] + (f" ({count} instances)" if count != 4096 else ""),
-                   "instances": count, "sum_kappa": int(sum(h.kappa for h in hs)),
-                   "sum_n": int(sum(h.n for h in hs)), "size_classes": int(ncls),
-                   "class_launch_configs": cfg.tolist(), "l2": "inputs larger than L2",
-                   "classes": "one union (HM_ONE_CLASS)" if args.one_class else "size classes by kappa (factors of 4)"},
-        "instances_per_s": count * world * args.steps / (t_max / 1e3),
-        "time_to_matching_ms": {"median": statistics.median(step_ms), "mean": t_ms / len(step_ms),
-                                "p99": float(np.percentile(step_ms, 99))},
-        "create_s": t_create, "generate_s": t_gen,
-        "plain_per_instance": None if plain_ms is None else {
-            "ms": plain_ms, "value": units_step / (plain_ms / 1e3), "unit": "pins/s",
-            "batched_speedup": plain_ms / (t_ms / args.steps)},
-        "clocks": clk, "cpu_baseline": None, "e2e": None,
+                   "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+        "batch": r, "clocks": clk, "cpu_baseline": None, "e2e": None,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -446,33 +583,36 @@ def run_batch(args, world, rank, local):
 
 # ------------------------------------------------------------------ serving arm
 
-def run_serve(args, world, rank, local):
-    """Requests arrive as a Poisson stream at each rate of the sweep and go
-    through hm_server (continuous batching); latency = submit -> done."""
+def serve_pool(seed: int, scale: int = 1):
     import torch
     import synth
-    import paper_2602_22976_gb300 as hm
-
-    import torch.distributed as dist
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    hm.build()
-    seed = replica_seed(args.seed, rank)
     rng = np.random.default_rng(seed)
-    pool_n = max(8, 128 // args.scale)
-    kap = np.exp(rng.uniform(np.log(1e3), np.log(1e7 / args.scale), size=pool_n)).astype(np.int64)
+    pool_n = max(8, 128 // scale)
+    kap = np.exp(rng.uniform(np.log(1e3), np.log(1e7 / scale), size=pool_n)).astype(np.int64)
     pool = [synth.serve_request(int(k), seed=seed * 100_000 + i) for i, k in enumerate(kap)]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     arrays = [(pin(h.eoff), pin(h.pins), pin(h.weights)) for h in pool]
+    return pool, arrays, kap
+
+
+def measure_serve(seed: int, rates, count_for, scale: int = 1, slots: int = 8, arrival_seed: int = 1) -> dict:
+    """Requests drawn from a pool of serving-shaped hypergraphs arrive as a
+    Poisson stream at each rate and go through hm_server (continuous
+    batching); latency = submit -> done. Then the whole stream at once,
+    served with `slots` slots against one slot (one request at a time, each
+    through the hm_solve_host path)."""
+    import paper_2602_22976_gb300 as hm
+    import synth
+    pool, arrays, kap = serve_pool(seed, scale)
+    pool_n = len(pool)
     units = []  # kappa * rounds of every pool request (from a solo run)
     for h in pool:
         r = hm.solve_host(h)
         units.append(h.kappa * r.rounds)
 
-    def run(rate, count, slots):
-        arr = synth.arrivals(count, rate, seed=args.seed + int(rate))
-        with hm.Server(slots=slots) as srv:
+    def run(rate, count, nslots):
+        arr = synth.arrivals(count, rate, seed=arrival_seed + int(min(rate, 1e6)))
+        with hm.Server(slots=nslots) as srv:
             t0 = time.perf_counter()
             tickets = []
             for i, ta in enumerate(arr):
@@ -487,39 +627,52 @@ def run_serve(args, world, rank, local):
             wall = time.perf_counter() - t0
             st = srv.stats()
         work = float(sum(units[k] for k, _ in tickets))
-        return {"rate_req_s": rate, "requests": count, "slots": slots,
+        return {"rate_req_s": rate, "requests": count, "slots": nslots,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "pins_per_s": work / wall, "req_per_s": count / wall, "work": work, "wall_s": wall,
                 "peak_inflight": st["peak_inflight"], "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9}
 
-    slots = 8
-    sweep = []
+    sweep = [run(rate, max(16, count_for(rate) // max(1, scale)), slots) for rate in rates]
+    served = run(1e9, 2 * pool_n, slots)
+    serial = run(1e9, 2 * pool_n, 1)
+    return {"pool": pool_n, "kappa_mean": float(kap.mean()), "slots": slots, "sweep": sweep,
+            "saturated_served": served, "saturated_one_slot": serial,
+            "served_speedup": served["pins_per_s"] / serial["pins_per_s"],
+            "h2d_bytes_per_request": int(np.mean([h.eoff.nbytes + h.pins.nbytes + h.weights.nbytes
+                                                  for h in pool]))}
+
+
+def run_serve(args, world, rank, local):
+    """Requests arrive as a Poisson stream at each rate of the sweep and go
+    through hm_server (continuous batching); latency = submit -> done."""
+    import torch
+    import paper_2602_22976_gb300 as hm
+
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hm.build()
+    seed = replica_seed(args.seed, rank)
     clocks = Clocks(local)
     clocks.start()
-    for rate in (100, 300, 1000, 3000, 10000):
-        count = int(min(max(64, rate * 1.0), 1000) // max(1, args.scale))
-        sweep.append(run(rate, max(count, 16), slots))
-    clk = clocks.stop()
-    # saturated throughput: the whole pool at once, served vs one request at a time
     if world > 1:
         dist.barrier()
-    served = run(1e9, 2 * pool_n, slots)
+    r = measure_serve(seed, (100, 300, 1000, 3000, 10000), lambda rate: int(min(max(64, rate), 1000)),
+                      args.scale, arrival_seed=args.seed)
+    clk = clocks.stop()
+    served = r["saturated_served"]
     work_all, wall_max = replica_totals(served["work"], served["wall_s"] * 1e3, world)
-    serial = run(1e9, 2 * pool_n, 1)
     out = {
         "metric": METRIC, "value": work_all / (wall_max / 1e3), "unit": "pins/s", "n_gpus": world,
-        "steps": 2 * pool_n, "warmup": 0, "ms_per_step": 1e3 / served["req_per_s"],
+        "steps": served["requests"], "warmup": 0, "ms_per_step": 1e3 / served["req_per_s"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS["serve"]["desc"], "pool": pool_n, "slots": slots,
-                   "kappa_mean": float(kap.mean()), "l2": "inputs larger than L2"},
-        "sweep": sweep, "saturated_served": served, "saturated_one_slot": serial,
-        "served_speedup": served["pins_per_s"] / serial["pins_per_s"],
-        "clocks": clk, "cpu_baseline": None,
+        "config": {"workload": WORKLOADS["serve"]["desc"], "l2": "inputs larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "serve": r, "clocks": clk, "cpu_baseline": None,
         "e2e": {"value": served["pins_per_s"], "unit": "pins/s",
-                "h2d_bytes_per_step": int(np.mean([h.eoff.nbytes + h.pins.nbytes + h.weights.nbytes
-                                                   for h in pool])),
-                "d2h_bytes_per_step": None},
+                "h2d_bytes_per_step": r["h2d_bytes_per_request"], "d2h_bytes_per_step": None},
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -598,8 +751,9 @@ def run_ours(args, world, rank, local):
     else:
         alg_bytes, bytes_model = kb[dom], "this design's per-unit counts (kernel_bytes)"
     achieved = alg_bytes / (prof[dom][0] / 1e3) / 1e9
-    # the DRAM bytes the kernel actually moved (ncu, committed summary) over the same time
-    traffic = measured_traffic(dom, rnd_mode, args.workload)
+    # the DRAM bytes the kernels actually moved (ncu, committed rows) over the same time
+    design_pl = {k: kb[k] / max(1, prof[k][1]) for k in ("init", "argmax", "win", "kill")}
+    traffic = measured_traffic(dom, rnd_mode, args.workload, design_pl[dom])
     traffic_gbs = traffic * prof[dom][1] / (prof[dom][0] / 1e3) / 1e9 if traffic else None
     per_kernel = {k: {"ms": prof[k][0], "launches": prof[k][1], "alg_bytes": kb[k],
                       "gbs": (kb[k] / (prof[k][0] / 1e3) / 1e9) if prof[k][0] > 0 else None}
@@ -607,11 +761,34 @@ def run_ours(args, world, rank, local):
     round_ms = [[round(float(x), 4) for x in row[:3]] for row in prof["rounds_ms"]]
     total_bytes = sum(kb.values())
     # random-access ceilings of this GPU for an array the size of the live flags
-    ra = hm.probe_random_access(max(h.m, 1 << 20), 200_000_000)
+    ra = probe_random_access(max(h.m, 1 << 20), 200_000_000, stream.cuda_stream or None)
     kills = float(stats[:, hm.STAT_COLUMNS.index("kills")].sum())
     rar = random_access_roofline(stats, prof, ra, rnd_mode)
     loop_ms = sum(prof[k][0] for k in hm.KERNELS)
-    rounds_run = int(prof["argmax"][1])
+    rounds_run = int(prof["win"][1])  # one win launch a round (the argmax step is three kernels when re-randomised)
+    # the whole match: the method's bytes of steps a1-a4 (the plain
+    # formulation), this design's element bytes, and the DRAM bytes ncu
+    # counted (committed rows), each over the timed match
+    t_match_s = t_max / args.steps / 1e3
+    mb = method_match_bytes(stats) if stats[:, 10].sum() > 0 else None  # HM_STAT_LEDGES, from the replay
+    dram = {k: measured_traffic(k, rnd_mode, args.workload, design_pl[k]) for k in ("init", "argmax", "win", "kill")}
+    dram_total = (sum(dram[k] * prof[k][1] if k != "init" else dram[k] for k in dram)
+                  if all(v is not None for v in dram.values()) else None)
+    frac = lambda b: None if b is None else b / t_match_s / 1e9 / measured_peaks()["hbm_gbs"]
+    whole = {
+        "t_match_ms": t_match_s * 1e3,
+        "model_bytes": None if mb is None else mb["total"], "model_bytes_by_step": mb,
+        "model_frac": frac(None if mb is None else mb["total"]),
+        "design_bytes": total_bytes, "design_frac": frac(total_bytes),
+        "dram_bytes": dram_total, "dram_frac": frac(dram_total),
+        "dram_bytes_by_kernel": {k: (None if dram[k] is None else dram[k] * (prof[k][1] if k != "init" else 1))
+                                 for k in dram},
+        "peak_gbs": measured_peaks()["hbm_gbs"],
+        "note": ("bytes per match over the timed match time and the measured HBM peak: model = the method's "
+                 "steps a1-a4 as the plain formulation moves them (per-round units from the replay's "
+                 "counters); design = this design's element bytes (kernel_bytes); dram = ncu's "
+                 "dram__bytes per launch (profiles/traffic.json) times launches"),
+    }
     # init + three kernels per round (argmax, win, kill with the round end);
     # five in the re-randomised rounds (the argmax step is three kernels there)
     launches = 1 + (5 if rnd_mode else 3) * rounds_run
@@ -681,7 +858,7 @@ def run_ours(args, world, rank, local):
             parity = bool(np.array_equal(o.edges, res.edges) and o.rounds == res.rounds)
             cpu = {"value": h.kappa * o.rounds / tc, "unit": "pins/s", "cores": cpu_cores_used(),
                    "kind": "oracle", "sample": f"the full instance, one oracle run ({tc:.1f} s)",
-                   "active_pins": int(o.round_stats[:, 1].sum())}
+                   "active_pins": int(o.round_stats[:, 1].sum()), "host": host_cpu()}
             if not rnd_mode:
                 # the paper's single-core Greedy baseline: sort by priority, take an
                 # edge when all its pins are free (same order, so the same matching)
@@ -694,6 +871,27 @@ def run_ours(args, world, rank, local):
                               "speedup_of_match": tg * 1e3 / gpu_ms}
                 if e2e:
                     cpu_greedy["speedup_end_to_end"] = tg * 1e3 / e2e["ms_per_step"]
+        # the batching and serving workloads, measured in the same run on the
+        # same GPU (one GPU only: the scaling runs report the main metric)
+        sub_batch = sub_serve = None
+        if world == 1 and args.workload == "large" and not rnd_mode and args.scale == 1:
+            mt.close()  # the batch below needs the room more than this handle
+            clocks2 = Clocks(local)
+            clocks2.start()
+            if not args.no_batch:
+                sub_batch = measure_batch(args.seed, 4096, steps=10, warmup=3, stream=stream)
+                sub_batch["note"] = ("4,096 instances in one graph launch (10 timed launches, CUDA events) "
+                                     "against the same instances as 4,096 hm_match launches (median of 3)")
+            if not args.no_serve:
+                sub_serve = measure_serve(args.seed, (1000, 10000), lambda rate: min(rate, 1000),
+                                          arrival_seed=args.seed)
+                sub_serve["note"] = ("Poisson arrivals at 1,000 and 10,000 req/s (1,000 requests each); "
+                                     "saturated = the whole stream submitted at once, 8 slots against one "
+                                     "slot (one request at a time through hm_solve_host)")
+            clk2 = clocks2.stop()
+            for x in (sub_batch, sub_serve):
+                if x is not None:
+                    x["clocks"] = clk2
         out = {
             "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -716,13 +914,17 @@ def run_ours(args, world, rank, local):
                          "design_frac": design_gbs / peaks["hbm_gbs"],
                          "kernel_source": kernel_source_hash(TRAFFIC_ROWS[(dom, rnd_mode)][1]),
                          "peak_source": peaks["source"],
-                         "loop_gbs": total_bytes / (loop_ms / 1e3) / 1e9},
+                         "loop_gbs": total_bytes / (loop_ms / 1e3) / 1e9,
+                         "whole_match_model_frac": whole["model_frac"],
+                         "whole_match_design_frac": whole["design_frac"],
+                         "whole_match_dram_frac": whole["dram_frac"]},
             "random_access": {
                 "array_bytes": max(h.m, 1 << 20), "ceiling_gops": ra,
                 "kill_entries_gops": kills / (prof["kill"][0] / 1e3) / 1e9,
                 "note": "kill reads each target flag (rounds >= 2) and writes the live ones; "
                         "its bound is the random 1-byte load/store rate, not HBM bandwidth"},
             "random_access_roofline": rar,
+            "whole_match": whole,
             "kernels": per_kernel,
             "round_ms_argmax_win_kill": round_ms,
             "round_stats": stats.tolist(),
@@ -732,11 +934,14 @@ def run_ours(args, world, rank, local):
             "clocks": clk,
             "gpu_launches": launches * args.steps,
             "parity_vs_oracle": parity,
+            "batch": sub_batch,
+            "serve": sub_serve,
+            "paper_context": PAPER_CONTEXT,
         }
         if cpu and cpu.get("active_pins"):
             out["active_pins_per_s"] = cpu["active_pins"] * args.steps * world / (t_max / 1e3)
         print(json.dumps(out), flush=True)
-    mt.close()
+    mt.close()  # a no-op when the sub-measurements closed it already
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -28,8 +28,9 @@
  *    thread-local, NUL-terminated message describing the first problem.
  *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream). Work is enqueued on it in stream order.
- *  - Device pointers must be device-accessible memory of the current CUDA
- *    device; host pointers must be ordinary host memory unless stated.
+ *  - Device pointers must be memory of the current CUDA device (or managed
+ *    memory); memory of another GPU is refused with HM_EINVAL. Host
+ *    pointers must be ordinary host memory unless stated.
  *  - A handle is bound to the device that was current at hm_create.
  *  - No entry point traps or aborts on bad input; nothing is printed.
  */
@@ -220,7 +221,12 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
                                 of the vertices kept (HM_STAT_NEXT: the unmatched
                                 vertices with a live edge at the start of the
                                 round); 0 after hm_match */
-#define HM_STATS_COLS     10
+#define HM_STAT_LEDGES   10  /* after hm_profile_match only (a counting kernel it runs
+                                before each round's timed kernels): edges live at the
+                                start of the round; 0 after hm_match */
+#define HM_STAT_LPINS    11  /* after hm_profile_match only: sum of |e| over those
+                                edges; 0 after hm_match */
+#define HM_STATS_COLS     12
 /* Returns the number of rows written in *rows_out. Errors: HM_EINVAL. */
 hm_status hm_round_stats(hm_handle *h, int64_t *stats, int32_t max_rounds, int32_t *rows_out);
 
@@ -267,25 +273,6 @@ hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int6
 hm_status hm_create_ms(hm_handle *h, double *ms_out);
 
 /*
- * hm_probe_random_access - measure this GPU's rate of random single-element
- * accesses (no counterpart in the paper). The round kernels gather and
- * scatter 1-byte flags and 4-byte counters at random; their ceiling is this
- * rate, not streaming bandwidth. Runs `ops` accesses of each kind at
- * pseudo-random indices of a DEVICE scratch array of `array_bytes` bytes
- * (allocated and freed here, stream-ordered on `cuda_stream`; 1 KiB .. 4 GiB)
- * and writes the best of two timed runs, in 1e9 accesses per second, to
- * HOST double[HM_PROBE_COUNT]. Waits for completion.
- * Errors: HM_EINVAL, HM_ENOMEM, HM_ECUDA.
- */
-#define HM_PROBE_STORE1  0  /* 1-byte store */
-#define HM_PROBE_LOAD1   1  /* 1-byte load (L2, bypassing L1) */
-#define HM_PROBE_LOAD4   2  /* 4-byte load (L2, bypassing L1) */
-#define HM_PROBE_RED4    3  /* 4-byte atomic subtract, result unused */
-#define HM_PROBE_ATOMIC4 4  /* 4-byte atomic subtract returning the old value */
-#define HM_PROBE_COUNT   5
-hm_status hm_probe_random_access(uint64_t array_bytes, uint64_t ops, double *gops_out, void *cuda_stream);
-
-/*
  * hm_solve_host - one call from HOST buffers to HOST result: copies eoff,
  * pins, weights (host memory; pinned memory gives full link bandwidth) to
  * the device on `cuda_stream`, runs hm_create + hm_match + hm_result and
@@ -308,10 +295,10 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
  * hm_match_noalloc - match one small hypergraph with one kernel launch and
  * no memory allocation at all. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they
- * need a matching - for example code that is capturing a CUDA graph on its
- * stream (cudaMalloc would break the capture), a framework that hands out
- * all device memory from its own arena, or a latency-bound loop that cannot
- * afford cudaMalloc's synchronisation. The caller passes inputs and outputs;
+ * need a matching - for example a framework that hands out all device
+ * memory from its own arena and allows no other allocator, or a
+ * latency-bound loop that cannot afford cudaMalloc's synchronisation. The
+ * caller passes inputs and outputs;
  * the working memory is a fixed 8 MiB array declared once in the library
  * (every GPU that loads libhm.so reserves it until the process exits).
  *
@@ -332,7 +319,8 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
  * clears the parts it uses, so calls whose kernels overlap on the GPU
  * (different streams, or several host threads) race and corrupt each other;
  * serialise them. Errors returned directly: HM_EINVAL (sizes, flags, NULL or
- * host pointers), HM_ECUDA (symbol lookup or launch failure).
+ * host pointers, or memory of another device than the current one),
+ * HM_ECUDA (symbol lookup or launch failure).
  */
 hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff, const int32_t *pins,
                            const float *weights, uint64_t seed, uint32_t flags,

@@ -26,14 +26,15 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
                 5: "HM_EBUSY"}
 HM_UNWEIGHTED, HM_BORROW_INPUT, HM_VALIDATE, HM_AUTOTUNE, HM_ONE_CLASS = 0x1, 0x2, 0x4, 0x8, 0x10
 HM_VERTEX_MATCHED, HM_VERTEX_NONE = -1, -2
-STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills", "items", "next", "live", "deg")
+STAT_COLUMNS = ("active", "advance", "proposals", "winners", "winpins", "kills", "items", "next", "live", "deg",
+                "ledges", "lpins")
 KERNELS = ("init", "argmax", "win", "kill", "round_end")
 
 # Every entry point of include/hm.h, in declaration order.
 ENTRY_POINTS = ("hm_create", "hm_match", "hm_set_round_cap", "hm_set_noise", "hm_launch_config", "hm_autotune",
                 "hm_result", "hm_result_device",
                 "hm_round_stats", "hm_vertex_state", "hm_profile_match", "hm_create_ms",
-                "hm_probe_random_access", "hm_solve_host", "hm_match_noalloc", "hm_batch_create",
+                "hm_solve_host", "hm_match_noalloc", "hm_batch_create",
                 "hm_batch_match", "hm_batch_result", "hm_batch_info", "hm_batch_destroy",
                 "hm_server_create", "hm_server_submit", "hm_server_wait", "hm_server_stats",
                 "hm_server_destroy", "hm_last_error", "hm_destroy")
@@ -77,7 +78,6 @@ def lib() -> ctypes.CDLL:
             "hm_vertex_state": ([p, p], i32),
             "hm_profile_match": ([p, p, p, p, p, i32], i32),
             "hm_create_ms": ([p, p], i32),
-            "hm_probe_random_access": ([u64, u64, p, p], i32),
             "hm_solve_host": ([i64, i64, p, p, p, u64, u32, p, p, p, p, p], i32),
             "hm_match_noalloc": ([i64, i64, p, p, p, u64, u32, p, p, p], i32),
             "hm_batch_create": ([p, i32, p, p, p, p, p, u64, u32, p], i32),
@@ -404,17 +404,6 @@ class Server:
             self.close()
         except Exception:
             pass
-
-
-PROBES = ("store1B", "load1B", "load4B", "red4B", "atomic4B")
-
-
-def probe_random_access(array_bytes: int, ops: int = 200_000_000, stream=None) -> dict:
-    """Random single-element access rates of this GPU (1e9 per second)."""
-    out = np.zeros(len(PROBES), dtype=np.float64)
-    _check(lib().hm_probe_random_access(int(array_bytes), int(ops), out.ctypes.data,
-                                        _stream_handle(stream)))
-    return dict(zip(PROBES, out.tolist()))
 
 
 def solve_host(hg, stream=None, allow=(HM_OK,)) -> Result:

@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhm.so")
 BUILD = os.path.join(HERE, "_build")
+# the benchmark's random-access probe: its own library, not part of libhm.so
+PROBE_SRC = os.path.join(HERE, "probe", "probe.cu")
+PROBE_LIB = os.path.join(HERE, "probe", "libhmprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -71,6 +74,20 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_probe(force: bool = False) -> str:
+    """Compile libhmprobe.so (the benchmark's random-access probe) if stale."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), "-shared", PROBE_SRC, "-o", tmp] + ARCH +
+                       ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-cudart", "static"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
         st->lpack = st->live = st->kpack = st->sdeg = 0;
+        st->ledges = st->lpins = 0;
     }
 }
 
@@ -520,6 +521,35 @@ __global__ void __launch_bounds__(kT) k_kept_degrees(RoundArgs a, int random) {
     block_add_u64(sum, s_red, &st->sdeg);
 }
 
+// Statistics of the per-kernel replay only, launched before a round's timed
+// kernels: the edges live at the start of the round and the sum of their
+// sizes, added to the round's counters. A graph's edge is live while
+// neither endpoint is matched (its liveness is read from the matched flags
+// in both orders); a hypergraph's live flag is indexed by j in the fixed
+// order and by the input id in the re-randomised rounds.
+__global__ void __launch_bounds__(kT) k_live_edges(RoundArgs a, int random) {
+    __shared__ unsigned long long s_red[kT / 32];
+    unsigned long long ne = 0, np = 0;
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < a.m; j += (int64_t)gridDim.x * kT) {
+        bool live;
+        int64_t size;
+        if (a.pairs) {
+            const int2 e = __ldg(reinterpret_cast<const int2 *>(a.pinsj) + j);
+            live = a.vmatch[e.x] == 0 && a.vmatch[e.y] == 0;
+            size = 2;
+        } else {
+            live = a.alive[random ? __ldg(a.order + j) : (int32_t)j] != 0;
+            size = a.eoffj[j + 1] - a.eoffj[j];
+        }
+        if (live) {
+            ne += 1;
+            np += (unsigned long long)size;
+        }
+    }
+    block_add_u64(ne, s_red, &a.st->ledges);
+    block_add_u64(np, s_red, &a.st->lpins);
+}
+
 // a2: each warp takes 32 winners of the round at a time (warp_win). The
 // winners' vertex records were completed by the argmax kernel.
 __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
@@ -544,7 +574,8 @@ __global__ void __launch_bounds__(kT) k_win(RoundArgs a) {
 __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t active, uint32_t nw,
                             uint32_t next, unsigned long long adv, unsigned long long props,
                             unsigned long long winpins, unsigned long long kills, uint32_t items,
-                            unsigned long long live, unsigned long long sdeg) {
+                            unsigned long long live, unsigned long long sdeg, unsigned long long ledges,
+                            unsigned long long lpins) {
     if (r - 1 < kStatRounds) {
         int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
         row[HM_STAT_ACTIVE] = active;
@@ -557,6 +588,8 @@ __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t act
         row[HM_STAT_NEXT] = next;
         row[HM_STAT_LIVE] = (int64_t)live;
         row[HM_STAT_DEG] = (int64_t)sdeg;
+        row[HM_STAT_LEDGES] = (int64_t)ledges;
+        row[HM_STAT_LPINS] = (int64_t)lpins;
     }
     int cont = 0;
     if (st->fault) {
@@ -587,12 +620,13 @@ __device__ void round_end(const RoundArgs &a) {
     const int64_t active = r == 1 ? a.n : (int64_t)st->cnt[par];
     const unsigned long long kp = st->kpack;
     const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, kp >> 32,
-                                  (uint32_t)kp, st->live, st->sdeg);
+                                  (uint32_t)kp, st->live, st->sdeg, st->ledges, st->lpins);
     st->nwin = 0;
     st->kdone = 0;
     st->rgrab = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
     st->lpack = st->live = st->kpack = st->sdeg = 0;
+    st->ledges = st->lpins = 0;
     if (cont) {
         st->round = r + 1;
         st->parity = par ^ 1;
@@ -833,6 +867,10 @@ void launch_win_kill_end(const Handle *h, const RoundArgs &a, cudaStream_t s, cu
     launch_win_kill(h, a, s, ev, kill_stride);
 }
 
+void launch_live_edges(const Handle *h, const RoundArgs &a, cudaStream_t s, int random) {
+    k_live_edges<<<grid_for((uint64_t)std::max<int64_t>(h->m, 1), kT, h->sm_count, 8), kT, 0, s>>>(a, random);
+}
+
 void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int random) {
     cudaEventRecord(ev[5], s);  // the end of the argmax span
     k_kept_degrees<<<grid_for((uint64_t)h->nregions * 32, kT, h->sm_count, 8), kT, 0, s>>>(a, random);
@@ -1042,6 +1080,7 @@ hm_status profile_match(Handle *h, cudaStream_t s, double *ms, int64_t *launches
     ms[HM_K_INIT] += t;
     launches[HM_K_INIT] += 1;
     for (int32_t r = 0;; ++r) {
+        launch_live_edges(h, a, s, 0);  // untimed: before the round's first event
         launch_round(h, a, s, ev);
         cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);

@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
         st->lpack = st->live = st->kpack = st->sdeg = 0;
+        st->ledges = st->lpins = 0;
     }
 }
 
@@ -666,6 +667,7 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
     ms[HM_K_INIT] += t;
     launches[HM_K_INIT] += 1;
     for (int32_t r = 0;; ++r) {
+        launch_live_edges(h, a, s, 1);  // untimed: before the round's first event
         launch_rround(h, a, s, ev);
         cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);

@@ -21,18 +21,21 @@ def test_reference_arm_line():
     same metric, unit and workload as the GPU arm, the oracle as its
     cpu_baseline, and an e2e object without host copies."""
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
-                         timeout=600, cwd=ROOT)
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=900, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "pins/s"
     assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
-    assert d["steps"] == 1 and d["warmup"] == 1
+    assert d["steps"] == 1 and d["warmup"] == 0
     assert d["config"]["workload"] == bench.WORKLOADS["large"]["desc"]
+    assert d["config"]["same_instance_as_gpu_arm"] is True  # the full instance, not a sample
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["cpu_baseline"]["host"]["nproc"] >= 1
+    assert "76.6x" in d["paper_context"]["claim"]
     assert d["e2e"] == {"value": d["value"], "unit": "pins/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
@@ -44,29 +47,72 @@ def _fake_root(tmp_path, source_text, rows):
     (csrc / "rrounds.cu").write_text(source_text + "// other file\n")
     prof = tmp_path / "profiles"
     prof.mkdir()
-    table = ["| kernel | mode | source hash | bytes per launch | launches |", "|---|---|---|---|---|"]
-    table += [f"| {k} | {m} | {h} | {b} | 11 |" for k, m, h, b in rows]
-    (prof / "traffic.md").write_text("\n".join(table) + "\n")
+    doc = {"rows": [dict(kernel=k, mode=m, workload=w, source_hash=h, bytes_per_launch=b, launches=11,
+                         scale=sc, design_bytes_per_launch=d) for k, m, w, h, b, sc, d in rows]}
+    (prof / "traffic.json").write_text(json.dumps(doc))
 
 
 def test_traffic_rows_keyed_by_source_workload_and_mode(tmp_path, monkeypatch):
     """A stored DRAM figure is reported only for the source it was measured
-    on, in its mode and on its workload; anything else reads as None."""
+    on, in its mode and on its workload; anything else reads as None. A row
+    captured at a smaller scale is scaled by this design's bytes per launch
+    at the bench's size over those of the captured run; a full-size row is
+    preferred to a scaled one."""
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h1 = hashlib.sha256(b"// kernel v1\n").hexdigest()[:16]
     h1r = hashlib.sha256(b"// kernel v1\n// other file\n").hexdigest()[:16]
     _fake_root(tmp_path, "// kernel v1\n", [
-        ("k_argmax", "fixed", h1, 1000), ("k_argmax", "fixed, graph", h1, 2000),
-        ("k_kill", "re-randomised", h1, 3000), ("k_rargmax+k_rlong+k_rfin", "re-randomised", h1r, 4000),
-        ("k_win", "fixed", "0000000000000000", 5000)])
+        ("k_argmax", "fixed", "large", h1, 1000, 1, None), ("k_argmax", "fixed", "graph", h1, 2000, 1, None),
+        ("k_argmax", "fixed", "large", h1, 111, 4, 50.0),
+        ("k_kill", "re-randomised", "large", h1, 3000, 1, None),
+        ("k_rargmax+k_rlong+k_rfin", "re-randomised", "large", h1r, 4000, 1, None),
+        ("k_win", "fixed", "large", "0000000000000000", 5000, 1, None),
+        ("k_kill", "fixed", "large", h1, 600, 4, 200.0)])
     assert bench.measured_traffic("argmax", False) == 1000.0
     assert bench.measured_traffic("argmax", False, "graph") == 2000.0
     assert bench.measured_traffic("argmax", False, "unweighted") is None
     assert bench.measured_traffic("kill", True) == 3000.0
     assert bench.measured_traffic("argmax", True) == 4000.0
     assert bench.measured_traffic("win", False) is None  # measured on another source
+    assert bench.measured_traffic("kill", False) is None  # scaled row, no design bytes to scale by
+    assert bench.measured_traffic("kill", False, "large", 800.0) == 600.0 * 800.0 / 200.0
     (tmp_path / "paper_2602_22976_gb300" / "csrc" / "rounds.cu").write_text("// kernel v2\n")
     assert bench.measured_traffic("argmax", False) is None  # the kernel changed since
+
+
+def test_committed_traffic_file_is_well_formed():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        doc = json.load(f)
+    assert doc["rows"]
+    for r in doc["rows"]:
+        assert r["mode"] in ("fixed", "re-randomised") and r["bytes_per_launch"] > 0
+        assert len(r["source_hash"]) == 16 and r.get("scale", 1) >= 1
+        assert (r["kernel"], r["mode"] == "re-randomised") in {(v[0], k[1]) for k, v in bench.TRAFFIC_ROWS.items()}
+
+
+def test_method_match_bytes_from_the_counters():
+    """The plain formulation's bytes of steps a1-a4 from the per-round units:
+    active vertices (NEXT) and their degrees (DEG), live edges (LEDGES) and
+    live pins (LPINS), winners and their pins."""
+    stats = np.zeros((2, 12), dtype=np.int64)
+    stats[:, 7] = [10, 4]        # active vertices
+    stats[:, 9] = [100, 30]      # their degree sums
+    stats[:, 10] = [20, 6]       # live edges
+    stats[:, 11] = [90, 25]      # live pins
+    stats[:, 3] = [5, 2]         # winners
+    stats[:, 4] = [20, 7]        # their pins
+    stats[:, 1] = 999            # other columns play no part
+    b = bench.method_match_bytes(stats)
+    assert b["a1"] == 24 * 14 + 8 * 130
+    assert b["a2"] == 24 * 26 + 8 * 115 + 27 + 7
+    assert b["a3"] == 5 * 115 + 4 * 26
+    assert b["a4"] == 8 * (26 + 14)
+    assert b["total"] == b["a1"] + b["a2"] + b["a3"] + b["a4"]
+
+
+def test_host_cpu_reports_cores():
+    h = bench.host_cpu()
+    assert h["nproc"] >= 1 and h["machine"]
 
 
 def test_method_argmax_bytes_from_the_counters():

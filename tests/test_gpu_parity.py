@@ -283,11 +283,46 @@ def test_solve_host_rejects_bad_input(n, m):
 
 
 def test_random_access_probe():
-    r = hmlib.probe_random_access(1 << 20, 2_000_000)
-    assert set(r) == set(hmlib.PROBES) and all(v > 0 for v in r.values())
+    """The benchmark's probe library (not part of libhm.so) measures positive
+    rates and refuses a too-small array."""
+    import bench
+    r = bench.probe_random_access(1 << 20, 2_000_000)
+    assert set(r) == set(bench.PROBES) and all(v > 0 for v in r.values())
+    with pytest.raises(RuntimeError, match="array_bytes"):
+        bench.probe_random_access(10, 1)
+
+
+def test_busy_while_a_match_runs_on_another_stream():
+    """HM_EBUSY: a handle refuses a match, a profiled match and an autotune
+    on a second stream while its last match is still queued or running on
+    the first. The first stream is kept busy by ordinary memory fills queued
+    ahead of the match (no kernel waits on anything), so the match cannot
+    have finished when the second call is made a few microseconds later."""
+    h = synth.large(seed=2, n=500_000, m=1_000_000)
+    o = oracle.match(h)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     L = hmlib.lib()
-    out = np.zeros(5)
-    assert L.hm_probe_random_access(10, 1, out.ctypes.data, None) == EINVAL
+    with hmlib.Matcher.from_hypergraph(h) as mt:
+        mt.match(s1)  # builds the CUDA graph
+        torch.cuda.synchronize()
+        buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(s1):
+            for _ in range(100):  # about 100 x 0.15 ms of fills ahead of the match
+                buf.fill_(1)
+        mt.match(s1)
+        assert L.hm_match(mt.handle, s2.cuda_stream) == hmlib.HM_EBUSY
+        assert "another stream" in hmlib.last_error()
+        ms, launches = np.zeros(5), np.zeros(5, dtype=np.int64)
+        assert L.hm_profile_match(mt.handle, s2.cuda_stream, ms.ctypes.data, launches.ctypes.data,
+                                  None, 0) == hmlib.HM_EBUSY
+        cfg, t = np.zeros(4, dtype=np.int32), ctypes.c_double(0)
+        assert L.hm_autotune(mt.handle, s2.cuda_stream, cfg.ctypes.data, ctypes.byref(t)) == hmlib.HM_EBUSY
+        r = mt.result()  # waits for the match on s1
+        assert r.rounds == o.rounds and np.array_equal(r.edges, o.edges)
+        mt.match(s2)  # nothing in flight any more: the second stream is accepted
+        r = mt.result()
+        assert r.rounds == o.rounds and np.array_equal(r.edges, o.edges)
+        del buf
 
 
 # ------------------------------------------------------------------ errors
@@ -401,10 +436,13 @@ def test_active_vertices_and_their_degrees_per_round():
     """The argmax step's count of the vertices it keeps (HM_STAT_NEXT) and the
     replay's count of their degrees (HM_STAT_DEG) equal, round by round, the
     active vertex sets of the oracle's run and their degree sums, in the
-    fixed order and in re-randomised rounds. A plain match leaves the degree
-    column at 0."""
+    fixed order and in re-randomised rounds; the replay's live edges and
+    live pins at the start of every round (HM_STAT_LEDGES, HM_STAT_LPINS)
+    equal the oracle's. A plain match leaves these three columns at 0."""
     nxt = hmlib.STAT_COLUMNS.index("next")
     dg = hmlib.STAT_COLUMNS.index("deg")
+    le = hmlib.STAT_COLUMNS.index("ledges")
+    lp = hmlib.STAT_COLUMNS.index("lpins")
     cases = [synth.large(seed=5, n=300_000, m=600_000), synth.small(seed=3),
              synth.unweighted(seed=2, n=100_000, m=200_000), synth.rgg(seed=4, n=50_000),
              synth.from_edges(7, [[0, 1], [1, 2], [2, 3], [3, 4]], None, seed=1)]
@@ -422,8 +460,12 @@ def test_active_vertices_and_their_degrees_per_round():
             stats = mt.round_stats()
         assert res.status == OK and res.rounds == o.rounds
         assert plain[:o.rounds, nxt].tolist() == u and not plain[:, dg].any()
+        assert not plain[:, le].any() and not plain[:, lp].any()
         assert stats[:o.rounds, nxt].tolist() == u
         assert stats[:o.rounds, dg].tolist() == sdeg
+        assert stats[:o.rounds, le].tolist() == o.round_stats[:, 0].tolist()
+        assert stats[:o.rounds, lp].tolist() == o.round_stats[:, 1].tolist()
+        assert not stats[o.rounds:, le].any()  # the closing round finds no live edge
 
 
 @pytest.mark.parametrize("big_weight", [1.0, 1e-3])
