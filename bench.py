@@ -197,11 +197,13 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
                # write; kill range: item write
             winb = row[WIN] * (16 + 4 + 1) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 8
         if random:  # list + record; scanned entry = entry + flag; live entry = id/base
-                    # record + compacted write; proposal = record write, id map, offset
-                    # pair, counter read+write, clear of the previous one; kept = list write
+                    # record + compacted write; proposal = largest key written and read
+                    # back, kept-list read, record read + write, counter word read +
+                    # write (its size rides in it), clear of the previous count; kept =
+                    # list write; winner = its relabelled id
             b["argmax"] += (row[ACT] * ((4 if r else 0) + 16) + row[ADV] * (4 + 1)
-                            + row[LIVE] * (8 + 4) + row[PROP] * (16 + 4 + 16 + 8 + 4)
-                            + row[NEXT] * 4)
+                            + row[LIVE] * (8 + 4) + row[PROP] * (8 + 8 + 4 + 16 + 8 + 8 + 4)
+                            + row[NEXT] * 4 + row[WIN] * 4)
         elif pairs:
             if r == 0:  # first entry + its other endpoint + offset pair read, record write
                 b["argmax"] += row[ACT] * (4 + 4 + 16 + 16) + row[PROP] * 2 * pc + row[NEXT] * 4

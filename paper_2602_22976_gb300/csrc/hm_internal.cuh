@@ -157,9 +157,14 @@ struct RoundArgs {
     int32_t *vnbrR;             // graphs: the same for vadjR, compacted with it
     const int32_t *jof;         // input id -> j
     uint32_t *P2;               // second proposal counter buffer
+    int t_input;                // T[v] holds input edge ids (re-randomised rounds), not j
+    int w64;                    // proposal words are 64-bit (some edge has more than 65535 pins)
+    const uint32_t *S32;        // |e| << 16 by input id: the proposal words' start value
+    const unsigned long long *S64;  // |e| << 32 (w64)
+    unsigned long long *W64a, *W64b;  // 64-bit proposal words by round parity (w64)
     int2 *lq;                   // long lists of the round: {vertex, first chunk}
-    unsigned long long *lbest;  // their largest key of the round
-    uint32_t lq_cap;            // capacity of lq / lbest
+    unsigned long long *rbest;  // every active vertex's largest key of the round
+    uint32_t lq_cap;            // capacity of lq
 };
 
 struct Handle {
@@ -207,10 +212,13 @@ struct Handle {
     int32_t *vnbrR = nullptr;   // graphs: working copy, compacted with vadjR
     int32_t *jof = nullptr;
     uint32_t *P2 = nullptr;
+    uint32_t *S32 = nullptr;              // |e| << 16 by input id (every edge <= 65535 pins)
+    unsigned long long *S64 = nullptr;    // |e| << 32 by input id (otherwise)
+    unsigned long long *W64a = nullptr, *W64b = nullptr;
     int2 *lq = nullptr;
-    unsigned long long *lbest = nullptr;
+    unsigned long long *rbest = nullptr;  // re-randomised rounds: largest key of the round per vertex
     uint32_t lq_cap = 0;
-    unsigned rargmax_grid = 0, rlong_grid = 0;
+    unsigned rargmax_grid = 0, rlong_grid = 0, rpropose_grid = 0;
     cudaGraphExec_t exec_rand = nullptr;
     int64_t graph_cap_rand = -1;
     LaunchConfig graph_cfg_rand;

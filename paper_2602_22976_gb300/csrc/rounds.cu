@@ -309,6 +309,7 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
     const int lane = threadIdx.x & 31;
     uint32_t len = 0;
     int64_t b = 0;
+    int32_t ein = -1;
     if (j >= 0) {
         if (a.graph) {  // d = 2: the pins sit at 2j, 2j + 1
             b = 2 * (int64_t)j;
@@ -317,7 +318,7 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
             b = __ldg(a.eoffj + j);
             len = (uint32_t)(__ldg(a.eoffj + j + 1) - b);
         }
-        const int32_t ein = __ldg(a.order + j);
+        ein = __ldg(a.order + j);
         a.inM[ein] = 1;
         if (a.wround) a.wround[ein] = r;
         winpins += len;
@@ -336,7 +337,7 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
     const uint32_t total = __shfl_sync(kFull, inc, 31);
     const unsigned lt = lanemask_lt();
     for (uint32_t p0 = 0; p0 < total; p0 += 32 * U) {
-        int32_t v[U], jk[U];
+        int32_t v[U], jk[U];  // jk: the winner as T[v] names it (j, or its input id when a.t_input)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t q = p0 + 32 * u + lane;
@@ -347,7 +348,7 @@ __device__ __forceinline__ void warp_win(const RoundArgs &a, int r, int32_t j, u
                 const uint32_t e = __shfl_sync(kFull, exc, k + d);
                 if (e <= q) k += d;
             }
-            jk[u] = __shfl_sync(kFull, j, k);
+            jk[u] = __shfl_sync(kFull, a.t_input ? ein : j, k);
             const int64_t bk = __shfl_sync(kFull, b, k);
             const uint32_t ek = __shfl_sync(kFull, exc, k);
             v[u] = q < total ? __ldg(a.pinsj + bk + (q - ek)) : -1;
@@ -752,12 +753,13 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
 
 // vmatch (graphs in the fixed order, else null): the matched flags, which
 // there stand in for T[v] = kCurMatched.
+// order null: T[v] holds input ids already (the re-randomised rounds).
 __global__ void k_vertex_state(const int4 *vrec, const uint8_t *vmatch, const int32_t *order, int64_t n,
                                int32_t *out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = vmatch && vmatch[v] ? kCurMatched : vrec[v].x;
-        out[v] = j >= 0 ? order[j] : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
+        out[v] = j >= 0 ? (order ? order[j] : j) : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
     }
 }
 
@@ -1172,8 +1174,8 @@ hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_m
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
     const int4 *vrec = h->last_random ? h->vrecR : h->vrec;
     const uint8_t *vmatch = h->vmatch;  // graphs (both orders): the matched flags
-    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(vrec, vmatch, h->order, h->n,
-                                                                               out_dev);
+    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(
+        vrec, vmatch, h->last_random ? nullptr : h->order, h->n, out_dev);
     return cudaGetLastError();
 }
 

@@ -20,26 +20,28 @@
 // reads vadjE and writes the compacted lists to the working copy (vadjR);
 // later rounds compact vadjR in place. Lists are scheduled by length:
 //   - at most kLong entries: the 32 vertices of a warp tile are scanned as
-//     one concatenated sequence, kU steps of 32 entries at a time (all their
-//     loads in flight together; segmented maximum and ballot compaction),
-//     so short and medium lists keep every lane busy;
+//     one concatenated sequence, each lane taking kE consecutive entries of
+//     a batch (scan_tile: per-list maxima folded in shared memory, one warp
+//     scan per batch for the compaction offsets), so short and medium lists
+//     keep every lane busy;
 //   - longer lists: queued with their chunk count (one 64-bit atomic hands
 //     out the queue slot and the first chunk); k_rlong scans the chunks of
 //     kChunk entries with one warp each and combines them per list with a
-//     64-bit atomicMax; k_rfin turns each list's maximum into the vertex's
-//     proposal. Long lists are not compacted: they are scanned from vadjE,
+//     64-bit atomicMax. Long lists are not compacted: they are scanned from vadjE,
 //     and their part of vadjR (read by the kill step) is copied once when
 //     the handle first runs this mode and never written.
 // Proposals use the P counter of Alg. 1 counted up and double-buffered by
-// round parity: a vertex adds 1 to P_r[T[v]], the edge wins when the count
-// reaches |e|, and the vertex clears the entry it counted in the previous
-// round in the other buffer, which the next round reuses. Every vertex that
-// proposed a still-live edge is active in the next round and clears it;
-// stale counts are left only on dead edges, which nobody proposes again.
-// The clear is a plain store: all vertices of a large edge clear the same
-// word, and same-address stores cost far less than same-address atomics
-// (an undo by atomic add measured 5-30 % slower per round). T[v] and the
-// winner list hold relabelled ids j.
+// round parity, indexed by input edge id and packed with the edge's size
+// (propose): a vertex adds 1 to P_r[T[v]] and learns from the same atomic
+// whether the count reached |e| (the edge wins); it clears the count it
+// added in the previous round in the other buffer, which the next round
+// reuses. Every vertex that proposed a still-live edge is active in the
+// next round and clears it; stale counts are left only on dead edges, which
+// nobody proposes again. T[v] holds the input id; the winner list holds
+// relabelled ids j (looked up for the winners only). The scans leave each
+// vertex's largest key of the round in rbest; k_rpropose then makes all
+// proposals of the round, one vertex per thread, so a proposal's random
+// access is not on the scans' critical path.
 // The win kernel and the kill kernel (which ends the round) of rounds.cu
 // run on this handle's re-randomised vertex records and lists: the cursor
 // field stays 0, so the kill range of a matched vertex is its whole
@@ -63,7 +65,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kLong = 2048;   // lists longer than this are scanned in chunks
 constexpr uint32_t kChunk = 2048;  // entries per chunk of a long list
 constexpr uint32_t kSeqMax = 64;   // graphs, round 1: tiles whose lists are all this short go one list per lane
-constexpr int kU = 4;              // 32-entry steps with loads in flight together
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
@@ -96,18 +97,25 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
     __syncthreads();
 }
 
-// key_r(e) of input edge e whose base priority is `base`. The product and
-// the sum are rounded separately (no fused multiply-add), as the
-// definition's float32 operations are.
-__device__ __forceinline__ unsigned long long round_key_of(uint64_t s0, float scale, int r, uint32_t e, float base) {
-    const uint64_t x = splitmix64_at(s0, ((uint64_t)(uint32_t)r << 32) + e + 1u);
+// key_r(e) of input edge e whose base priority is `base`: p_r(e) = base +
+// scale * U_r(e), the product and the sum rounded separately (no fused
+// multiply-add), as the definition's float32 operations are. U_r(e) comes
+// from output number (r << 32) + e + 1 of the SplitMix64 stream started at
+// s0, computed in fewer operations than splitmix64_at: cr = s0 + ((r << 32)
+// + 1) * gamma (one value per round), so that output's state is cr + e *
+// gamma; and the output's last step, x ^ (x >> 31), leaves bits 33..63
+// unchanged, so the top 24 bits are those of x itself.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+__device__ __forceinline__ uint64_t round_counter_base(uint64_t s0, int r) {
+    return s0 + ((((uint64_t)(uint32_t)r) << 32) + 1u) * kGamma;
+}
+__device__ __forceinline__ unsigned long long scan_key(uint64_t cr, float scale, uint32_t e, float base) {
+    uint64_t x = cr + (uint64_t)e * kGamma;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
     const float u = __uint2float_rn((uint32_t)(x >> 40));
     const float p = __fadd_rn(base, __fmul_rn(u, scale));
     return ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(0xFFFFFFFFu - e);
-}
-
-__device__ __forceinline__ unsigned long long round_key(const RoundArgs &a, int r, uint32_t e, float base) {
-    return round_key_of(a.noise_s0, a.noise_scale, r, e, base);
 }
 
 // Round 1 of a graph, a tile whose lists are all short: each lane takes the
@@ -117,9 +125,10 @@ __device__ __forceinline__ unsigned long long round_key(const RoundArgs &a, int 
 __device__ __noinline__ unsigned long long first_round_max(const int2 *vadjE, int64_t lb, uint32_t len, uint64_t s0,
                                                            float scale) {
     unsigned long long best = 0;
+    const uint64_t cr = round_counter_base(s0, 1);
     for (uint32_t i = 0; i < len; ++i) {
         const int2 ev = __ldg(vadjE + lb + i);
-        const unsigned long long key = round_key_of(s0, scale, 1, (uint32_t)ev.x, __int_as_float(ev.y));
+        const unsigned long long key = scan_key(cr, scale, (uint32_t)ev.x, __int_as_float(ev.y));
         if (key > best) best = key;
     }
     return best;
@@ -129,26 +138,28 @@ __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
     return (int32_t)(0xFFFFFFFFu - (uint32_t)k);
 }
 
-// Proposal of a vertex for edge j (relabelled id) in round r: counts in the
-// round's buffer; returns whether it completed the count (j wins).
-__device__ __forceinline__ bool propose(const RoundArgs &a, uint32_t *Pc, int32_t j) {
-    const uint32_t size = a.graph ? 2u : (uint32_t)(a.eoffj[j + 1] - a.eoffj[j]);
-    return atomicAdd(Pc + j, 1u) + 1u == size;
+// The P counter of round r for input edge e, packed with the edge's size:
+// word = (|e| << H) | count, H = 16 when no edge has more than 65535 pins
+// (two 32-bit buffers), else H = 32 (two 64-bit buffers). A proposal adds 1
+// and gets the size back with the old count from the same atomic, so no
+// other read is needed to see whether it completed the edge; the clear of
+// the previous round's count keeps the size half. The buffers start each
+// match as copies of the sizes (rand_init).
+__device__ __forceinline__ bool propose(const RoundArgs &a, int r, int32_t e) {
+    if (a.w64) {
+        unsigned long long *W = (r & 1) ? a.W64b : a.W64a;
+        const unsigned long long old = atomicAdd(W + e, 1ull);
+        return (old & 0xFFFFFFFFull) + 1ull == (old >> 32);
+    }
+    uint32_t *W = (r & 1) ? a.P2 : a.P;
+    const uint32_t old = atomicAdd(W + e, 1u);
+    return (old & 0xFFFFu) + 1u == (old >> 16);
 }
 
-// Appends the winners of a warp (lanes with w set, edge nb) to the list.
-__device__ __forceinline__ void append_winners(const RoundArgs &a, bool w, int32_t nb) {
-    const int lane = threadIdx.x & 31;
-    const unsigned wm = __ballot_sync(kFull, w);
-    if (!wm) return;
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.st->nwin, (uint32_t)__popc(wm));
-    base = __shfl_sync(kFull, base, 0);
-    if (w) {
-        const uint64_t idx = (uint64_t)base + __popc(wm & lanemask_lt());
-        if (idx < a.win_cap) a.win[idx] = nb;
-        else a.st->fault = 2;
-    }
+// Clears the count a vertex added to edge e in round r - 1 (its T then).
+__device__ __forceinline__ void clear_previous(const RoundArgs &a, int r, int32_t e) {
+    if (a.w64) atomicAnd(((r & 1) ? a.W64a : a.W64b) + e, 0xFFFFFFFF00000000ull);
+    else atomicAnd(((r & 1) ? a.P : a.P2) + e, 0xFFFF0000u);
 }
 
 __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
@@ -156,8 +167,15 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
     for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < total; i += (int64_t)gridDim.x * kT) {
         if (i < a.m) {
             a.alive[i] = 1;
-            a.P[i] = 0;
-            a.P2[i] = 0;
+            if (a.w64) {
+                const unsigned long long z = __ldg(a.S64 + i);
+                a.W64a[i] = z;
+                a.W64b[i] = z;
+            } else {
+                const uint32_t z = __ldg(a.S32 + i);
+                a.P[i] = z;
+                a.P2[i] = z;
+            }
             a.inM[i] = 0;
         }
         if (i < a.n) {
@@ -208,12 +226,159 @@ __device__ __noinline__ void flush_winners(const RoundArgs &a, uint64_t base, ui
     }
 }
 
+constexpr int kE = 4;  // consecutive entries a lane takes per batch of the tile scan
+
+// Per-warp tile state of the scan in shared memory: for each lane's vertex
+// (its owner index) the start and end of its list in the tile's
+// concatenated sequence, the list's first entry in memory, the running
+// maximum key and live count, and the tile's live count before the list
+// (compaction offsets).
+struct TileSmem {
+    uint32_t pre[32], end[32], base[32], gst[32], live[32];
+    unsigned long long best[32];
+};
+
+// The short and medium lists of a tile of 32 vertices (L = list length of
+// this lane's vertex, 0 when it takes no part; lb = its first entry), read
+// as one concatenated sequence in batches of 32 * kE entries: lane l takes
+// the kE consecutive positions from batch start + l * kE, finds the list
+// holding its first one by a binary search over the lists' starts, and
+// walks on (a run rarely crosses more than one list end). Each lane keeps
+// the maximum key and live count of every list piece in its run and folds
+// them into the list's shared entries with one atomic per piece. From round
+// 2 on the live entries are compacted: a warp scan of the lanes' live counts
+// gives every entry its place among the tile's live entries, and the live
+// count at each list's start (recorded by the lane holding that start)
+// turns it into the place in the list's own compacted copy. All reads of a
+// batch precede its writes (__syncwarp), and compacted entries land at or
+// before the positions they were read from, so compaction in place is safe.
+// Returns the list's maximum key (0: nothing live) and live count.
+template <bool kPairs>
+__device__ __forceinline__ void scan_tile(const RoundArgs &a, int r, const int2 *src, int2 *dst,
+                                          const int32_t *nsrc, int32_t *ndst, uint32_t L, uint32_t lb,
+                                          TileSmem &sm, unsigned long long &best, uint32_t &live,
+                                          unsigned long long &scanned) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t inc = warp_inclusive_scan(L);
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
+    best = 0;
+    live = 0;
+    if (total == 0) return;  // warp-uniform
+    sm.pre[lane] = inc - L;
+    sm.end[lane] = inc;
+    sm.base[lane] = lb;
+    sm.best[lane] = 0;
+    sm.live[lane] = 0;
+    __syncwarp();
+    uint32_t gbase = 0;  // live entries of the tile before this batch
+    const uint64_t cr = round_counter_base(a.noise_s0, r);
+    for (uint32_t s0 = 0; s0 < total; s0 += 32 * kE) {
+        const uint32_t p0 = s0 + (uint32_t)lane * kE;
+        // the list holding p0: the largest x with pre[x] <= p0 (a non-empty
+        // list whenever p0 < total)
+        int x = 0;
+#pragma unroll
+        for (int bit = 16; bit; bit >>= 1)
+            if (sm.pre[x + bit] <= p0) x += bit;
+        int own[kE];
+        bool lv[kE], first[kE];
+        int2 ev[kE];
+        int32_t nb[kE];
+        {
+            int o = x;
+            uint32_t cend = sm.end[o], cpre = sm.pre[o], cbase = sm.base[o];
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const uint32_t p = p0 + k;
+                const bool valid = p < total;
+                if (valid)
+                    while (p >= cend) {  // past this list's end (empty lists end where they start)
+                        ++o;
+                        cend = sm.end[o];
+                        cpre = sm.pre[o];
+                        cbase = sm.base[o];
+                    }
+                own[k] = o;
+                first[k] = valid && p == cpre;
+                const uint64_t at = (uint64_t)cbase + (p - cpre);
+                // plain loads: from round 3 on this kernel rewrites the lists behind the reads
+                ev[k] = valid ? src[at] : make_int2(0, 0);
+                if (kPairs) nb[k] = valid ? nsrc[at] : 0;
+                lv[k] = valid;
+            }
+        }
+        if (r > 1) {
+#pragma unroll
+            for (int k = 0; k < kE; ++k)
+                lv[k] = lv[k] && (kPairs ? __ldg(a.vmatch + nb[k]) == 0 : __ldg(a.alive + ev[k].x) != 0);
+        }
+        // the run's pieces: maximum key and live count per list, each piece
+        // folded into its list's shared entries with one atomic
+        uint32_t lcnt = 0;
+        {
+            unsigned long long m = 0;
+            uint32_t c = 0;
+            int co = own[0];
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                if (own[k] != co) {
+                    if (c) {
+                        atomicMax(&sm.best[co], m);
+                        atomicAdd(&sm.live[co], c);
+                    }
+                    co = own[k];
+                    m = 0;
+                    c = 0;
+                }
+                if (lv[k]) {
+                    const unsigned long long key = scan_key(cr, a.noise_scale, (uint32_t)ev[k].x,
+                                                            __int_as_float(ev[k].y));
+                    m = key > m ? key : m;
+                    ++c;
+                }
+                lcnt += lv[k] ? 1u : 0u;
+            }
+            scanned += p0 < total ? min(total - p0, (uint32_t)kE) : 0u;
+            if (c) {
+                atomicMax(&sm.best[co], m);
+                atomicAdd(&sm.live[co], c);
+            }
+        }
+        if (r > 1) {  // compaction
+            const uint32_t incl = warp_inclusive_scan(lcnt);
+            const uint32_t g0 = gbase + incl - lcnt;  // live entries of the tile before this lane's run
+            uint32_t g = g0;
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                if (first[k]) sm.gst[own[k]] = g;
+                g += lv[k] ? 1u : 0u;
+            }
+            __syncwarp();  // every read of this batch and every list start precede the writes
+            g = g0;
+#pragma unroll
+            for (int k = 0; k < kE; ++k)
+                if (lv[k]) {
+                    const uint64_t at = (uint64_t)sm.base[own[k]] + (g - sm.gst[own[k]]);
+                    dst[at] = ev[k];
+                    if (kPairs) ndst[at] = nb[k];
+                    ++g;
+                }
+            gbase += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+    }
+    best = sm.best[lane];
+    live = sm.live[lane];
+    __syncwarp();  // the next tile rewrites the shared state
+}
+
 // a1 of a re-randomised round for the vertices of the active list. The
 // regions are those of the fixed-order loop; warps of a persistent grid
 // take them one at a time from a counter, so that regions with long lists
 // do not leave other warps idle.
 template <bool kPairs>
 __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
+    __shared__ TileSmem s_tile[kT / 32];
     DevState *st = a.st;
     const int r = st->round;
     const int par = st->parity;
@@ -221,8 +386,6 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     int32_t *out = par ? a.list0 : a.list1;
     const uint32_t *cnt_in = a.lcnt + (size_t)par * a.nregions;
     uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
-    uint32_t *Pc = (r & 1) ? a.P2 : a.P;  // counts of this round
-    uint32_t *Po = (r & 1) ? a.P : a.P2;  // counts of the previous round
     // round 1 keeps every entry: it reads the immutable lists and writes
     // nothing; round 2 compacts them into the working copy; later rounds
     // compact the working copy in place
@@ -232,7 +395,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     int32_t *ndst = a.vnbrR;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    unsigned long long scanned = 0, props = 0, nlive = 0;
+    unsigned long long scanned = 0, nlive = 0;
     for (;;) {
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(&st->rgrab, 1u);
@@ -246,7 +409,7 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
         } else {
             count = cnt_in[g];
         }
-        uint32_t kept = 0, won = 0;
+        uint32_t kept = 0;
         for (uint32_t i0 = 0; i0 < count; i0 += 32) {
             const uint32_t i = i0 + lane;
             const bool ok = i < count;
@@ -259,12 +422,9 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                 const uint32_t nch = ((uint32_t)rec.w + kChunk - 1) / kChunk;
                 const unsigned long long old = atomicAdd(&st->lpack, (1ull << 32) | nch);
                 const uint32_t slot = (uint32_t)(old >> 32);
-                if (slot < a.lq_cap) {
-                    a.lq[slot] = make_int2(v, (int32_t)(uint32_t)old);
-                    a.lbest[slot] = 0;
-                } else {
-                    st->fault = 3;
-                }
+                if (slot < a.lq_cap) a.lq[slot] = make_int2(v, (int32_t)(uint32_t)old);
+                else st->fault = 3;
+                a.rbest[v] = 0;  // k_rlong folds the chunks' maxima in
             }
             // the short and medium lists of the tile as one sequence
             const uint32_t L = act && !lng ? (uint32_t)rec.w : 0u;
@@ -281,93 +441,19 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
                 live = L;
                 scanned += L;
             } else {
-            const uint32_t inc = warp_inclusive_scan(L);
-            const uint32_t pre = inc - L;
-            const uint32_t total = __shfl_sync(kFull, inc, 31);
-            for (uint32_t s0 = 0; s0 < total; s0 += 32 * kU) {
-                int o[kU];
-                uint32_t opre[kU];
-                int64_t ob[kU];
-                int2 ev[kU];
-                int32_t nbv[kU];  // graphs: the other endpoint of each entry
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    // owner of position p: the largest lane x with pre_x <= p
-                    // (it has L_x > 0 when p < total)
-                    const uint32_t p = s0 + 32 * u + lane;
-                    int x = 0;
-#pragma unroll
-                    for (int bit = 16; bit; bit >>= 1) {
-                        const uint32_t pc = __shfl_sync(kFull, pre, x + bit);
-                        if (pc <= p) x += bit;
-                    }
-                    o[u] = x;
-                    opre[u] = __shfl_sync(kFull, pre, x);
-                    ob[u] = (int64_t)(uint32_t)__shfl_sync(kFull, rec.z, x);
-                }
-                // plain loads: from round 3 on this kernel rewrites the lists behind the reads
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const uint32_t p = s0 + 32 * u + lane;
-                    ev[u] = p < total ? src[ob[u] + (int64_t)(p - opre[u])] : make_int2(0, 0);
-                    if (kPairs) nbv[u] = p < total ? nsrc[ob[u] + (int64_t)(p - opre[u])] : 0;
-                }
-                bool lvv[kU];
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const uint32_t p = s0 + 32 * u + lane;
-                    lvv[u] = p < total &&
-                             (r == 1 || (kPairs ? __ldg(a.vmatch + nbv[u]) == 0 : __ldg(a.alive + ev[u].x) != 0));
-                }
-                __syncwarp();  // every read of this batch precedes its compaction writes
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const uint32_t su = s0 + 32 * u;
-                    if (su < total) {  // warp-uniform
-                        const bool lv = lvv[u];
-                        const unsigned long long key =
-                            lv ? round_key(a, r, (uint32_t)ev[u].x, __int_as_float(ev[u].y)) : 0ull;
-                        // lanes [sst, lane) of this step hold earlier entries of the same list
-                        const uint32_t sst = opre[u] > su ? opre[u] - su : 0u;
-                        const unsigned seg_lt = lt & ~((1u << sst) - 1u);
-                        const unsigned lm = __ballot_sync(kFull, lv);
-                        const uint32_t carried = __shfl_sync(kFull, live, o[u]);
-                        if (lv && r > 1) {  // compaction
-                            dst[ob[u] + carried + __popc(lm & seg_lt)] = ev[u];
-                            if (kPairs) ndst[ob[u] + carried + __popc(lm & seg_lt)] = nbv[u];
-                        }
-                        // segmented running maximum over the step
-                        unsigned long long mx = key;
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const unsigned long long y = __shfl_up_sync(kFull, mx, d);
-                            if (lane >= d && (uint32_t)(lane - d) >= sst && y > mx) mx = y;
-                        }
-                        // each owner takes the maximum at the last lane of its piece
-                        const bool mine = L > 0 && pre < su + 32 && pre + L > su;
-                        const uint32_t tail = mine ? min(pre + L - su, 32u) - 1u : (uint32_t)lane;
-                        const unsigned long long tmx = __shfl_sync(kFull, mx, (int)tail);
-                        if (mine) {
-                            if (tmx > best) best = tmx;
-                            const uint32_t lo = pre > su ? pre - su : 0u;
-                            const unsigned upto = tail == 31u ? kFull : ((2u << tail) - 1u);
-                            live += __popc(lm & upto & ~((1u << lo) - 1u));
-                        }
-                        scanned += su + lane < total ? 1u : 0u;
-                    }
-                }
+                scan_tile<kPairs>(a, r, src, dst, nsrc, ndst, L, (uint32_t)rec.z, s_tile[threadIdx.x >> 5], best,
+                                  live, scanned);
             }
-            }
-            bool keep = false, w = false;
-            int32_t nb = -1;
+            // the vertex's best key goes to k_rpropose, which makes every
+            // proposal of the round (a dependent chain of random reads that
+            // would otherwise sit in this scan's critical path)
+            bool keep = false;
             if (act && !lng) {
-                if (r > 1) Po[rec.x] = 0;  // T[v] of the previous round is what v counted there
+                if (r > 1) clear_previous(a, r, rec.x);  // T[v] of the previous round is what v counted there
+                a.rbest[v] = best;
                 if (best != 0) {
-                    nb = __ldg(a.jof + edge_of_key(best));
-                    a.vrec[v] = make_int4(nb, 0, rec.z, (int32_t)live);
-                    w = propose(a, Pc, nb);
+                    reinterpret_cast<int2 *>(a.vrec + v)[1] = make_int2(rec.z, (int32_t)live);
                     keep = true;
-                    ++props;
                     nlive += live;
                 } else {
                     reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurNone, 0);
@@ -376,21 +462,16 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
             const unsigned km = __ballot_sync(kFull, keep);
             if (keep) out[base + kept + __popc(km & lt)] = v;
             kept += __popc(km);
-            const unsigned lgm = __ballot_sync(kFull, lng);  // long lists stay; k_rfin may drop them
+            const unsigned lgm = __ballot_sync(kFull, lng);  // long lists stay; k_rpropose may drop them
             if (lng) out[base + kept + __popc(lgm & lt)] = v;
             kept += __popc(lgm);
-            const unsigned wm = __ballot_sync(kFull, w);
-            if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
-            won += __popc(wm);
         }
         if (lane == 0) {
             cnt_out[g] = kept;
             if (kept) atomicAdd(&st->cnt[par ^ 1], kept);
         }
-        if (won) flush_winners(a, base, won);
     }
     warp_add_u64(scanned, &st->adv);
-    warp_add_u64(props, &st->proposals);
     warp_add_u64(nlive, &st->live);
 }
 
@@ -414,16 +495,36 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
                 const uint32_t mid = (lo + hi + 1) >> 1;
                 if ((uint32_t)a.lq[mid].y <= c) lo = mid; else hi = mid - 1;
             }
-            const int2 q = a.lq[lo];
+            const int2 q = a.lq[lo];  // {vertex, its first chunk}
             const int4 rec = a.vrec[q.x];
             const int64_t lb = (int64_t)(uint32_t)rec.z;
             const int64_t b = lb + (int64_t)(c - (uint32_t)q.y) * kChunk;
             const int64_t e = min(lb + (int64_t)(uint32_t)rec.w, b + (int64_t)kChunk);
             unsigned long long mx = 0;
-            for (int64_t p = b + lane; p < e; p += 32) {
-                const int2 x = __ldg(a.vadjE + p);  // long lists are never compacted
+            const uint64_t cr = round_counter_base(a.noise_s0, r);
+            int64_t p = b + lane;
+            for (; p + 96 < e; p += 128) {  // four entries per lane in flight
+                int2 x[4];
+                bool lv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = __ldg(a.vadjE + p + 32 * u);  // long lists are never compacted
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    lv[u] = r == 1 || (kPairs ? __ldg(a.vmatch + __ldg(a.vnbrE + p + 32 * u)) == 0
+                                              : __ldg(a.alive + x[u].x) != 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (lv[u]) {
+                        const unsigned long long k = scan_key(cr, a.noise_scale, (uint32_t)x[u].x,
+                                                              __int_as_float(x[u].y));
+                        if (k > mx) mx = k;
+                        ++nlive;
+                    }
+            }
+            for (; p < e; p += 32) {
+                const int2 x = __ldg(a.vadjE + p);
                 if (r == 1 || (kPairs ? __ldg(a.vmatch + __ldg(a.vnbrE + p)) == 0 : __ldg(a.alive + x.x) != 0)) {
-                    const unsigned long long k = round_key(a, r, (uint32_t)x.x, __int_as_float(x.y));
+                    const unsigned long long k = scan_key(cr, a.noise_scale, (uint32_t)x.x, __int_as_float(x.y));
                     if (k > mx) mx = k;
                     ++nlive;
                 }
@@ -434,7 +535,7 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
                 if (y > mx) mx = y;
             }
             if (lane == 0) {
-                if (mx) atomicMax(a.lbest + lo, mx);
+                if (mx) atomicMax(a.rbest + q.x, mx);
                 scanned += (unsigned long long)(e - b);
             }
         }
@@ -443,40 +544,55 @@ __global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
     block_add_u64(nlive, s_red, &st->live);
 }
 
-// Proposals of the long lists (one thread per list).
-__global__ void __launch_bounds__(kT) k_rfin(RoundArgs a) {
+// Every proposal of the round: for each vertex the argmax step kept (one
+// warp per region of the kept list), its largest key of the round (rbest,
+// from the scan or from the chunks of a long list) names its new T[v]; the
+// vertex counts itself in P_r of that edge, and the count that completes the
+// edge makes it a winner. A long list with nothing live left drops out here
+// (T[v] = none; the vertex leaves the active count). Winners are staged per
+// region and appended with one atomic.
+__global__ void __launch_bounds__(kT) k_rpropose(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
-    const unsigned long long lp = st->lpack;
-    const uint32_t nl = (uint32_t)(lp >> 32);
+    const int r = st->round, par = st->parity;
+    const int32_t *out = par ? a.list0 : a.list1;
+    const uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
     unsigned long long props = 0;
-    if (nl <= a.lq_cap) {
-        const int r = st->round, par = st->parity;
-        uint32_t *Pc = (r & 1) ? a.P2 : a.P;
-        uint32_t *Po = (r & 1) ? a.P : a.P2;
-        const uint32_t stride = gridDim.x * kT;
-        // whole warps iterate, so that winners can be appended with ballots
-        for (uint32_t s0 = blockIdx.x * kT + (threadIdx.x & ~31u); s0 < nl; s0 += stride) {
-            const uint32_t s = s0 + (threadIdx.x & 31);
+    for (uint64_t g = warp; g < a.nregions; g += nwarps) {
+        const uint32_t c = cnt_out[g];
+        const uint64_t base = g * a.region;
+        uint32_t won = 0;
+        for (uint32_t i0 = 0; i0 < c; i0 += 32) {
+            const uint32_t i = i0 + lane;
             bool w = false;
             int32_t nb = -1;
-            if (s < nl) {
-                const int32_t v = a.lq[s].x;
-                const int32_t prev = a.vrec[v].x;
-                if (r > 1) Po[prev] = 0;
-                const unsigned long long k = a.lbest[s];
-                if (k == 0) {  // no live entry left: v leaves the active list
+            if (i < c) {
+                const int32_t v = out[base + i];
+                const unsigned long long best = a.rbest[v];
+                const int4 rec = a.vrec[v];
+                // a long list (never compacted: its length field stays above
+                // kLong) clears what it counted in the previous round here
+                if ((uint32_t)rec.w > kLong && r > 1) clear_previous(a, r, rec.x);
+                if (best == 0) {  // a long list with nothing live left
                     reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurNone, 0);
                     atomicSub(&st->cnt[par ^ 1], 1u);
                 } else {
-                    nb = __ldg(a.jof + edge_of_key(k));
-                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(nb, 0);
-                    w = propose(a, Pc, nb);
+                    const int32_t e = edge_of_key(best);  // T[v], input id
+                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(e, 0);
+                    w = propose(a, r, e);
+                    if (w) nb = __ldg(a.jof + e);  // winners are listed by relabelled id
                     ++props;
                 }
             }
-            append_winners(a, w, nb);
+            const unsigned wm = __ballot_sync(kFull, w);
+            if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
+            won += __popc(wm);
         }
+        if (won) flush_winners(a, base, won);
     }
     block_add_u64(props, s_red, &st->proposals);
 }
@@ -486,6 +602,17 @@ __global__ void __launch_bounds__(kT) k_rfin(RoundArgs a) {
 __global__ void __launch_bounds__(kT) k_pair_endpoints(const int2 *vpair, uint64_t kappa, int32_t *vnbrE) {
     for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += (uint64_t)gridDim.x * kT)
         vnbrE[i] = vpair[i].y;
+}
+
+// The proposal words' start value by input id: |e| in the upper half.
+__global__ void __launch_bounds__(kT) k_size_words(const int32_t *order, const int64_t *eoffj, int64_t m, int graph,
+                                                   uint32_t *S32, unsigned long long *S64) {
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
+        const int32_t e = __ldg(order + j);
+        const uint64_t size = graph ? 2u : (uint64_t)(eoffj[j + 1] - eoffj[j]);
+        if (S32) S32[e] = (uint32_t)size << 16;
+        else S64[e] = (unsigned long long)size << 32;
+    }
 }
 
 // Lists as {input edge id, bits(base priority)} pairs, both copies, and
@@ -526,8 +653,14 @@ RoundArgs rand_args(const Handle *h) {
     a.noise_s0 = splitmix64_first(h->seed);
     a.jof = h->jof;
     a.P2 = h->P2;
+    a.t_input = 1;
+    a.w64 = h->p16 ? 0 : 1;
+    a.S32 = h->S32;
+    a.S64 = h->S64;
+    a.W64a = h->W64a;
+    a.W64b = h->W64b;
     a.lq = h->lq;
-    a.lbest = h->lbest;
+    a.rbest = h->rbest;
     a.lq_cap = h->lq_cap;
     return a;
 }
@@ -549,7 +682,7 @@ void launch_rround(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEven
         k_rargmax<false><<<h->rargmax_grid, kT, 0, s>>>(a);
         k_rlong<false><<<h->rlong_grid, kT, 0, s>>>(a);
     }
-    k_rfin<<<(unsigned)h->sm_count, kT, 0, s>>>(a);
+    k_rpropose<<<h->rpropose_grid, kT, 0, s>>>(a);
     if (ev) launch_kept_degrees(h, a, s, ev, 1);
     launch_win_kill_end(h, a, s, ev, 2);
 }
@@ -597,6 +730,7 @@ hm_status build_graph_rand(Handle *h) {
 hm_status rand_prepare(Handle *h, cudaStream_t s) {
     h->rargmax_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_rargmax<true>) : fit_per_sm(k_rargmax<false>)));
     h->rlong_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_rlong<true>) : fit_per_sm(k_rlong<false>)));
+    h->rpropose_grid = (unsigned)(h->sm_count * fit_per_sm(k_rpropose));
     if (h->vrecR) return HM_OK;
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
     h->lq_cap = (uint32_t)(std::min<uint64_t>(n, h->kappa / kLong) + 1);
@@ -606,8 +740,12 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
         (st = dalloc(&h->vadjR, h->kappa, s, "re-randomised vertex lists")) != HM_OK ||
         (st = dalloc(&h->jof, m, s, "inverse edge order")) != HM_OK ||
         (st = dalloc(&h->P2, m, s, "second proposal counters")) != HM_OK ||
+        (h->p16 && (st = dalloc(&h->S32, m, s, "edge sizes")) != HM_OK) ||
+        (!h->p16 && ((st = dalloc(&h->S64, m, s, "edge sizes")) != HM_OK ||
+                     (st = dalloc(&h->W64a, m, s, "proposal counters")) != HM_OK ||
+                     (st = dalloc(&h->W64b, m, s, "proposal counters")) != HM_OK)) ||
         (st = dalloc(&h->lq, h->lq_cap, s, "long-list queue")) != HM_OK ||
-        (st = dalloc(&h->lbest, h->lq_cap, s, "long-list maxima")) != HM_OK ||
+        (st = dalloc(&h->rbest, n, s, "largest keys of the round")) != HM_OK ||
         (h->graph && ((st = dalloc(&h->vnbrE, h->kappa, s, "list endpoints")) != HM_OK ||
                       (st = dalloc(&h->vnbrR, h->kappa, s, "re-randomised list endpoints")) != HM_OK))) {
         free_rand_buffers(h);
@@ -618,6 +756,8 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
     if (m) {
         k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
             h->order, h->vadj, h->weighted ? h->weights : nullptr, h->m, h->kappa, h->vadjE, h->vadjR, h->jof);
+        k_size_words<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->m, h->graph ? 1 : 0,
+                                                                    h->S32, h->S64);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             free_rand_buffers(h);
@@ -686,7 +826,8 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
 }
 
 void free_rand_buffers(Handle *h) {
-    void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->lbest, h->vnbrE, h->vnbrR};
+    void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->rbest, h->vnbrE, h->vnbrR,
+                    h->S32, h->S64, h->W64a, h->W64b};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, h->cap_stream);
     h->vrecR = nullptr;
@@ -695,7 +836,11 @@ void free_rand_buffers(Handle *h) {
     h->jof = nullptr;
     h->P2 = nullptr;
     h->lq = nullptr;
-    h->lbest = nullptr;
+    h->rbest = nullptr;
+    h->S32 = nullptr;
+    h->S64 = nullptr;
+    h->W64a = nullptr;
+    h->W64b = nullptr;
     h->vnbrE = nullptr;
     h->vnbrR = nullptr;
     if (h->exec_rand) cudaGraphExecDestroy(h->exec_rand);
