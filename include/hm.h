@@ -143,9 +143,9 @@ hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
  * amplitude). The 1/d bound of Lemma 1 holds for the cardinality of the
  * matching (unweighted input) in this mode; with weights plus noise the
  * matching is locally maximal for the noisy priorities, not for w.
- * The first match with amplitude > 0 allocates 16*kappa + 16*n + 8*m bytes
- * more on the device plus 16 bytes per vertex of degree above 2048
- * (owned by the handle until hm_destroy).
+ * The first match with amplitude > 0 allocates 16*kappa + 24*n + 12*m bytes
+ * more on the device (20*m more when some edge has more than 65535 pins)
+ * plus 8 bytes per 2048 pins (owned by the handle until hm_destroy).
  * hm_autotune tunes the fixed-order loop and leaves the amplitude set.
  * Errors: HM_EINVAL (NULL handle, amplitude negative, NaN or infinite).
  */

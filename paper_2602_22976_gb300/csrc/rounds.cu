@@ -128,18 +128,21 @@ constexpr int kLaneSteps = 4;  // a lane walks at most 4 x 4 entries before its 
 
 // First live entry of vadj[c, end) within kLaneSteps steps of four entries
 // (their loads are independent, so a step costs two dependent memory trips).
-// Returns its position (j = the edge), end if the list ran out, or -1 if
-// the budget ran out first.
-__device__ __forceinline__ int64_t next_live_bounded(const int32_t *__restrict__ vadj,
-                                                     const uint8_t *__restrict__ alive, int64_t c,
-                                                     int64_t end, int32_t &j) {
+// Returns its position (j = the edge), or end if the list ran out; sets
+// `more` when the budget ran out first. List positions are below kappa <
+// 2^32, so they are kept in 32 bits (fewer registers: more warps resident).
+__device__ __forceinline__ uint32_t next_live_bounded(const int32_t *__restrict__ vadj,
+                                                      const uint8_t *__restrict__ alive, uint32_t c, uint32_t end,
+                                                      int32_t &j, bool &more) {
+    more = false;
 #pragma unroll 1
     for (int step = 0; step < kLaneSteps; ++step) {
         if (c >= end) return end;
+        const uint32_t left = end - c;
         const int32_t e0 = __ldg(vadj + c);
-        const int32_t e1 = c + 1 < end ? __ldg(vadj + c + 1) : -1;
-        const int32_t e2 = c + 2 < end ? __ldg(vadj + c + 2) : -1;
-        const int32_t e3 = c + 3 < end ? __ldg(vadj + c + 3) : -1;
+        const int32_t e1 = left > 1 ? __ldg(vadj + c + 1) : -1;
+        const int32_t e2 = left > 2 ? __ldg(vadj + c + 2) : -1;
+        const int32_t e3 = left > 3 ? __ldg(vadj + c + 3) : -1;
         const bool a0 = __ldg(alive + e0) != 0;
         const bool a1 = e1 >= 0 && __ldg(alive + e1) != 0;
         const bool a2 = e2 >= 0 && __ldg(alive + e2) != 0;
@@ -148,24 +151,28 @@ __device__ __forceinline__ int64_t next_live_bounded(const int32_t *__restrict__
         if (a1) { j = e1; return c + 1; }
         if (a2) { j = e2; return c + 2; }
         if (a3) { j = e3; return c + 3; }
+        if (left <= 4) return end;
         c += 4;
     }
-    return c >= end ? end : -1;
+    more = true;
+    return end;
 }
 
 // The same walk over a graph's pair list: entry c is live when the other
 // endpoint of its edge is unmatched (the list's own vertex is active, so it
 // is unmatched too). Returns the position, with j = the edge and o = that
-// endpoint; end or -1 as above.
-__device__ __forceinline__ int64_t next_live_pair(const int2 *__restrict__ vpair, const uint8_t *__restrict__ vmatch,
-                                                  int64_t c, int64_t end, int32_t &j, int32_t &o) {
+// endpoint; end and `more` as above.
+__device__ __forceinline__ uint32_t next_live_pair(const int2 *__restrict__ vpair, const uint8_t *__restrict__ vmatch,
+                                                   uint32_t c, uint32_t end, int32_t &j, int32_t &o, bool &more) {
+    more = false;
 #pragma unroll 1
     for (int step = 0; step < kLaneSteps; ++step) {
         if (c >= end) return end;
+        const uint32_t left = end - c;
         const int2 e0 = __ldg(vpair + c);
-        const int2 e1 = c + 1 < end ? __ldg(vpair + c + 1) : make_int2(-1, -1);
-        const int2 e2 = c + 2 < end ? __ldg(vpair + c + 2) : make_int2(-1, -1);
-        const int2 e3 = c + 3 < end ? __ldg(vpair + c + 3) : make_int2(-1, -1);
+        const int2 e1 = left > 1 ? __ldg(vpair + c + 1) : make_int2(-1, -1);
+        const int2 e2 = left > 2 ? __ldg(vpair + c + 2) : make_int2(-1, -1);
+        const int2 e3 = left > 3 ? __ldg(vpair + c + 3) : make_int2(-1, -1);
         const bool a0 = __ldg(vmatch + e0.y) == 0;
         const bool a1 = e1.y >= 0 && __ldg(vmatch + e1.y) == 0;
         const bool a2 = e2.y >= 0 && __ldg(vmatch + e2.y) == 0;
@@ -174,9 +181,11 @@ __device__ __forceinline__ int64_t next_live_pair(const int2 *__restrict__ vpair
         if (a1) { j = e1.x; o = e1.y; return c + 1; }
         if (a2) { j = e2.x; o = e2.y; return c + 2; }
         if (a3) { j = e3.x; o = e3.y; return c + 3; }
+        if (left <= 4) return end;
         c += 4;
     }
-    return c >= end ? end : -1;
+    more = true;
+    return end;
 }
 
 // a1 for one vertex per lane: T[v] <- the first live entry of v's list at
@@ -188,7 +197,7 @@ __device__ __forceinline__ int64_t next_live_pair(const int2 *__restrict__ vpair
 // records {T, absolute cursor, list end, other endpoint of T}.
 template <bool kPairs>
 __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok, int32_t v, int32_t &nb,
-                                              unsigned long long &adv) {
+                                              uint32_t &adv) {
     const int lane = threadIdx.x & 31;
     const int32_t *__restrict__ vadj = a.vadj;
     const int2 *__restrict__ vpair = a.vpair;
@@ -196,7 +205,7 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
     const uint8_t *__restrict__ vmatch = a.vmatch;
     bool keep = false, walk = false, coop = false;
     nb = -1;
-    int64_t vb = 0, from = 0, end = 0, cn = 0;
+    uint32_t vb = 0, from = 0, end = 0, cn = 0;
     int32_t jj = 0, oo = 0;
     if (ok && r == 1) {
         // every edge is live in round 1: T[v] is the first entry; the record
@@ -221,47 +230,48 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
                 keep = true;  // T[v] still live: unchanged
             } else {
                 if (kPairs) {
-                    from = (int64_t)(uint32_t)rec.y;
-                    end = (int64_t)(uint32_t)rec.z;
-                    cn = next_live_pair(vpair, vmatch, from + 1, end, jj, oo);
+                    from = (uint32_t)rec.y;
+                    end = (uint32_t)rec.z;
+                    cn = next_live_pair(vpair, vmatch, from + 1, end, jj, oo, coop);
                 } else {
-                    vb = (int64_t)(uint32_t)rec.z;
-                    end = vb + (int64_t)(uint32_t)rec.w;
-                    from = vb + rec.y;
-                    cn = next_live_bounded(vadj, alive, from + 1, end, jj);
+                    vb = (uint32_t)rec.z;
+                    end = vb + (uint32_t)rec.w;
+                    from = vb + (uint32_t)rec.y;
+                    cn = next_live_bounded(vadj, alive, from + 1, end, jj, coop);
                 }
                 walk = true;
-                coop = cn < 0;
             }
         }
     }
     unsigned cm = __ballot_sync(kFull, coop);
     while (cm) {
         const int src = __ffs(cm) - 1;
-        int64_t p = __shfl_sync(kFull, from, src) + 1 + 4 * kLaneSteps;
-        const int64_t e = __shfl_sync(kFull, end, src);
-        int64_t fpos = e;
+        uint32_t p = __shfl_sync(kFull, from, src) + 1 + 4 * kLaneSteps;
+        const uint32_t e = __shfl_sync(kFull, end, src);
+        uint32_t fpos = e;
         int32_t fj = 0, fo = 0;
         while (p < e) {
-            const int64_t q = p + lane;
+            const bool in = (uint32_t)lane < e - p;  // p + lane < e, without overflow
+            const uint32_t q = p + (uint32_t)lane;
             unsigned lm;
             int32_t ej, eo = 0;
             if (kPairs) {
-                const int2 x = q < e ? __ldg(vpair + q) : make_int2(-1, -1);
+                const int2 x = in ? __ldg(vpair + q) : make_int2(-1, -1);
                 ej = x.x;
                 eo = x.y;
                 lm = __ballot_sync(kFull, eo >= 0 && __ldg(vmatch + eo) == 0);
             } else {
-                ej = q < e ? __ldg(vadj + q) : -1;
+                ej = in ? __ldg(vadj + q) : -1;
                 lm = __ballot_sync(kFull, ej >= 0 && __ldg(alive + ej) != 0);
             }
             if (lm) {
                 const int f = __ffs(lm) - 1;
-                fpos = p + f;
+                fpos = p + (uint32_t)f;
                 fj = __shfl_sync(kFull, ej, f);
                 if (kPairs) fo = __shfl_sync(kFull, eo, f);
                 break;
             }
+            if (e - p <= 32) break;  // the list ran out
             p += 32;
         }
         if (lane == src) {
@@ -272,16 +282,16 @@ __device__ __forceinline__ bool argmax_vertex(const RoundArgs &a, int r, bool ok
         cm &= cm - 1;
     }
     if (walk && kPairs) {
-        adv += (unsigned long long)(cn - from);
+        adv += cn - from;
         if (cn < end) {
-            a.vrec[v] = make_int4(jj, (int32_t)(uint32_t)cn, (int32_t)(uint32_t)end, oo);
+            a.vrec[v] = make_int4(jj, (int32_t)cn, (int32_t)end, oo);
             nb = jj;
             keep = true;
         } else {
             a.vrec[v] = make_int4(kCurNone, 0, 0, -1);
         }
     } else if (walk) {
-        adv += (unsigned long long)(cn - from);
+        adv += cn - from;
         int2 *st2 = reinterpret_cast<int2 *>(a.vrec + v);
         if (cn < end) {
             st2[0] = make_int2(jj, (int32_t)(cn - vb));
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const uint32_t g = blockIdx.x * (kT / 32) + wib;
-    unsigned long long adv = 0, props = 0;
+    uint32_t adv = 0, props = 0;  // one thread's counts stay below kappa < 2^32
     uint32_t kept = 0, won = 0;
     if (g < a.nregions) {
         const uint64_t base = (uint64_t)g * a.region;
