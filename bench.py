@@ -303,7 +303,7 @@ TRAFFIC_ROWS = {
     ("win", False): ("k_win", "rounds.cu"),
     ("kill", False): ("k_kill", "rounds.cu"),
     ("init", True): ("k_rinit", "rrounds.cu"),
-    ("argmax", True): ("k_rargmax+k_rlong+k_rfin", "rrounds.cu"),
+    ("argmax", True): ("k_rargmax+k_rlong+k_rpropose", "rrounds.cu"),
     ("win", True): ("k_win", "rounds.cu"),
     ("kill", True): ("k_kill", "rounds.cu"),
 }
