@@ -144,8 +144,10 @@ hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
  * matching (unweighted input) in this mode; with weights plus noise the
  * matching is locally maximal for the noisy priorities, not for w.
  * The first match with amplitude > 0 allocates 16*kappa + 24*n + 12*m bytes
- * more on the device (20*m more when some edge has more than 65535 pins)
- * plus 8 bytes per 2048 pins (owned by the handle until hm_destroy).
+ * more on the device (20*m more when some edge has more than 65535 pins;
+ * 24*kappa + 24*n + 8*m for a graph, every edge with two pins) plus 8 bytes
+ * per 2048 pins and 4 bytes per 1024 pins (owned by the handle until
+ * hm_destroy).
  * hm_autotune tunes the fixed-order loop and leaves the amplitude set.
  * Errors: HM_EINVAL (NULL handle, amplitude negative, NaN or infinite).
  */

@@ -162,6 +162,8 @@ struct RoundArgs {
     const uint32_t *S32;        // |e| << 16 by input id: the proposal words' start value
     const unsigned long long *S64;  // |e| << 32 (w64)
     unsigned long long *W64a, *W64b;  // 64-bit proposal words by round parity (w64)
+    const int32_t *vchunk;      // round 1: the vertex owning list entry c * kFlatW, per flat chunk c
+    uint64_t kappa;             // list entries
     int2 *lq;                   // long lists of the round: {vertex, first chunk}
     unsigned long long *rbest;  // every active vertex's largest key of the round
     uint32_t lq_cap;            // capacity of lq
@@ -215,6 +217,7 @@ struct Handle {
     uint32_t *S32 = nullptr;              // |e| << 16 by input id (every edge <= 65535 pins)
     unsigned long long *S64 = nullptr;    // |e| << 32 by input id (otherwise)
     unsigned long long *W64a = nullptr, *W64b = nullptr;
+    int32_t *vchunk = nullptr;            // round 1's flat scan: vertex of every chunk's first entry
     int2 *lq = nullptr;
     unsigned long long *rbest = nullptr;  // re-randomised rounds: largest key of the round per vertex
     uint32_t lq_cap = 0;

@@ -64,7 +64,6 @@ constexpr int kT = 256;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kLong = 2048;   // lists longer than this are scanned in chunks
 constexpr uint32_t kChunk = 2048;  // entries per chunk of a long list
-constexpr uint32_t kSeqMax = 64;   // graphs, round 1: tiles whose lists are all this short go one list per lane
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
@@ -118,22 +117,6 @@ __device__ __forceinline__ unsigned long long scan_key(uint64_t cr, float scale,
     return ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(0xFFFFFFFFu - e);
 }
 
-// Round 1 of a graph, a tile whose lists are all short: each lane takes the
-// largest key of its own list, read from the immutable lists (every entry
-// is live in round 1, and nothing is written). Kept out of line so that the
-// tile path of k_rargmax keeps its own code.
-__device__ __noinline__ unsigned long long first_round_max(const int2 *vadjE, int64_t lb, uint32_t len, uint64_t s0,
-                                                           float scale) {
-    unsigned long long best = 0;
-    const uint64_t cr = round_counter_base(s0, 1);
-    for (uint32_t i = 0; i < len; ++i) {
-        const int2 ev = __ldg(vadjE + lb + i);
-        const unsigned long long key = scan_key(cr, scale, (uint32_t)ev.x, __int_as_float(ev.y));
-        if (key > best) best = key;
-    }
-    return best;
-}
-
 __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
     return (int32_t)(0xFFFFFFFFu - (uint32_t)k);
 }
@@ -144,8 +127,17 @@ __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
 // and gets the size back with the old count from the same atomic, so no
 // other read is needed to see whether it completed the edge; the clear of
 // the previous round's count keeps the size half. The buffers start each
-// match as copies of the sizes (rand_init).
+// match as copies of the sizes (k_rinit). A graph's edges all have two
+// pins: its counts are 8-bit, four to a 32-bit word, with no size beside
+// them (the count an edge reaches is at most 2), so the counters of m edges
+// take m bytes and stay in L2.
 __device__ __forceinline__ bool propose(const RoundArgs &a, int r, int32_t e) {
+    if (a.pairs) {  // graphs: every edge has two pins; four 8-bit counts a word, no size needed
+        uint32_t *W = (r & 1) ? a.P2 : a.P;
+        const int sh = (e & 3) * 8;
+        const uint32_t old = atomicAdd(W + (e >> 2), 1u << sh);
+        return ((old >> sh) & 0xFFu) == 1u;
+    }
     if (a.w64) {
         unsigned long long *W = (r & 1) ? a.W64b : a.W64a;
         const unsigned long long old = atomicAdd(W + e, 1ull);
@@ -158,7 +150,8 @@ __device__ __forceinline__ bool propose(const RoundArgs &a, int r, int32_t e) {
 
 // Clears the count a vertex added to edge e in round r - 1 (its T then).
 __device__ __forceinline__ void clear_previous(const RoundArgs &a, int r, int32_t e) {
-    if (a.w64) atomicAnd(((r & 1) ? a.W64a : a.W64b) + e, 0xFFFFFFFF00000000ull);
+    if (a.pairs) atomicAnd(((r & 1) ? a.P : a.P2) + (e >> 2), ~(0xFFu << ((e & 3) * 8)));
+    else if (a.w64) atomicAnd(((r & 1) ? a.W64a : a.W64b) + e, 0xFFFFFFFF00000000ull);
     else atomicAnd(((r & 1) ? a.P : a.P2) + e, 0xFFFF0000u);
 }
 
@@ -167,7 +160,12 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
     for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < total; i += (int64_t)gridDim.x * kT) {
         if (i < a.m) {
             a.alive[i] = 1;
-            if (a.w64) {
+            if (a.pairs) {  // four 8-bit counts a word
+                if (i < (a.m + 3) / 4) {
+                    a.P[i] = 0;
+                    a.P2[i] = 0;
+                }
+            } else if (a.w64) {
                 const unsigned long long z = __ldg(a.S64 + i);
                 a.W64a[i] = z;
                 a.W64b[i] = z;
@@ -180,6 +178,7 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         }
         if (i < a.n) {
             if (a.pairs) a.vmatch[i] = 0;
+            a.rbest[i] = 0;  // round 1 folds list pieces into it with atomicMax
             const int64_t b = a.voff[i], e = a.voff[i + 1];
             a.vrec[i] = make_int4(a.firstj[i], 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
         }
@@ -227,6 +226,9 @@ __device__ __noinline__ void flush_winners(const RoundArgs &a, uint64_t base, ui
 }
 
 constexpr int kE = 4;  // consecutive entries a lane takes per batch of the tile scan
+constexpr int kFlatC = 32;              // round 1: consecutive entries a lane takes per chunk
+constexpr uint64_t kFlatW = 32 * kFlatC;  // round 1: entries per warp chunk
+constexpr int kFlatSpan = 192;          // round 1: a chunk's vertex offsets staged in shared memory up to this many
 
 // Per-warp tile state of the scan in shared memory: for each lane's vertex
 // (its owner index) the start and end of its list in the tile's
@@ -237,6 +239,8 @@ struct TileSmem {
     uint32_t pre[32], end[32], base[32], gst[32], live[32];
     unsigned long long best[32];
 };
+// round 1 stages up to kFlatSpan vertex offsets in a warp's TileSmem
+static_assert(kFlatSpan * sizeof(uint32_t) <= sizeof(TileSmem), "the staged offsets must fit a warp's tile state");
 
 // The short and medium lists of a tile of 32 vertices (L = list length of
 // this lane's vertex, 0 when it takes no part; lb = its first entry), read
@@ -372,6 +376,122 @@ __device__ __forceinline__ void scan_tile(const RoundArgs &a, int r, const int2 
     __syncwarp();  // the next tile rewrites the shared state
 }
 
+// Round 1 of the re-randomised rounds: every entry is live, so each
+// vertex's largest key is a plain maximum over its whole list. The lists
+// (vadjE, in vertex order) are read as one flat array: a warp takes chunks
+// of kFlatW consecutive entries, each lane kFlatC of them (16-byte loads),
+// whatever lists they belong to. A lane finds the vertex of its first entry
+// by a binary search over the vertex offsets between the vertices owning
+// this chunk's and the next chunk's first entries (vchunk, built once), and
+// walks on through the lists its run touches. A list that lies wholly inside
+// the run is stored at once; a piece of a longer list is folded into the
+// vertex's largest key with a 64-bit atomicMax (rbest starts at 0), one per
+// warp when the whole chunk lies inside one list. The proposals follow in
+// k_rpropose; nothing else is written.
+template <bool kPairs>
+__device__ __forceinline__ void flat_round1(const RoundArgs &a, uint32_t *s_off) {
+    // list positions are below kappa < 2^32: 32-bit arithmetic throughout
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * (uint32_t)kT + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * (uint32_t)kT) >> 5;
+    const uint32_t kappa = (uint32_t)a.kappa;
+    const uint32_t nchunks = (uint32_t)((a.kappa + kFlatW - 1) / kFlatW);
+    const uint64_t cr = round_counter_base(a.noise_s0, 1);
+    const float scale = a.noise_scale;
+    for (uint32_t c = warp; c < nchunks; c += nwarps) {  // uniform in the warp
+        const uint32_t cb = c * (uint32_t)kFlatW;
+        const uint32_t p0 = cb + (uint32_t)lane * kFlatC;
+        // this lane's positions p0 .. p0 + len - 1 (none when p0 >= kappa);
+        // cb is a multiple of kFlatW below kappa <= 2^32 - 1, so p0 <=
+        // 2^32 - 32 does not wrap
+        const uint32_t len = p0 < kappa ? min((uint32_t)kFlatC, kappa - p0) : 0u;
+        // the chunk's vertices lie in [vlo, vhi]; when there are fewer than
+        // kFlatSpan of them their offsets are staged in this warp's shared
+        // array (the search and the walk then read shared memory)
+        const int32_t vlo = __ldg(a.vchunk + c);
+        const int32_t vhi = c + 1 < nchunks ? __ldg(a.vchunk + c + 1) : (int32_t)(a.n - 1);
+        const bool staged = vhi - vlo + 1 < kFlatSpan;  // uniform: offsets vlo .. vhi + 1 fit
+        __syncwarp();  // the previous chunk's reads of the shared array are done
+        if (staged) {
+            for (int32_t i = lane; i <= vhi - vlo + 1; i += 32) s_off[i] = (uint32_t)__ldg(a.voff + vlo + i);
+            __syncwarp();
+        }
+        auto vo = [&](int32_t v) -> uint32_t {
+            return staged ? s_off[v - vlo] : (uint32_t)__ldg(a.voff + v);
+        };
+        int32_t cur = 0;
+        uint32_t cs = 0, ce = 0;
+        if (len) {
+            // the vertex whose list holds p0: the largest v with voff[v] <= p0
+            // (its list is not empty: a later vertex with the same offset
+            // would be larger)
+            int32_t lo = vlo, hi = vhi;
+            while (lo < hi) {
+                const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+                if (vo(mid) <= p0) lo = mid;
+                else hi = mid - 1;
+            }
+            cur = lo;
+            cs = vo(cur);
+            ce = vo(cur + 1);
+        }
+        // a chunk inside one list (the lists of hubs): one atomic per warp
+        // (every lane takes part in every shuffle: none sits behind a condition)
+        const uint32_t cs0 = __shfl_sync(kFull, cs, 0), cs31 = __shfl_sync(kFull, cs, 31);
+        const uint32_t ce0 = __shfl_sync(kFull, ce, 0);
+        const bool one = cs0 == cs31 && len == (uint32_t)kFlatC && ce0 - cb >= (uint32_t)kFlatW;
+        const bool all_one = __all_sync(kFull, one);
+        unsigned long long m = 0;
+#pragma unroll 1
+        for (uint32_t k0 = 0; k0 < len; k0 += 8) {
+            int2 ev[8];
+            if (k0 + 8 <= len) {  // four 16-byte loads: p0 + k0 is even, so 16-byte aligned
+                const int4 *v4 = reinterpret_cast<const int4 *>(a.vadjE + p0 + k0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 x = __ldg(v4 + u);
+                    ev[2 * u] = make_int2(x.x, x.y);
+                    ev[2 * u + 1] = make_int2(x.z, x.w);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) ev[u] = k0 + u < len ? __ldg(a.vadjE + p0 + k0 + u) : make_int2(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (k0 + u >= len) break;
+                const uint32_t p = p0 + k0 + u;
+                if (!all_one)
+                    while (p >= ce) {  // the list of cur ends before p: store or fold its piece
+                        if (cs >= p0) a.rbest[cur] = m;  // the whole list lay inside this run
+                        else if (m) atomicMax(a.rbest + cur, m);
+                        m = 0;
+                        ++cur;
+                        cs = ce;
+                        ce = vo(cur + 1);
+                    }
+                const unsigned long long key = scan_key(cr, scale, (uint32_t)ev[u].x, __int_as_float(ev[u].y));
+                m = key > m ? key : m;
+            }
+        }
+        if (all_one) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(kFull, m, d);
+                m = y > m ? y : m;
+            }
+            if (lane == 0) atomicMax(a.rbest + cur, m);
+        } else if (len) {  // the run's last piece
+            if (cs >= p0 && ce - p0 <= len) a.rbest[cur] = m;
+            else if (m) atomicMax(a.rbest + cur, m);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // round 1 scans and finds live every entry
+        atomicAdd(&a.st->adv, (unsigned long long)a.kappa);
+        atomicAdd(&a.st->live, (unsigned long long)a.kappa);
+    }
+}
+
 // a1 of a re-randomised round for the vertices of the active list. The
 // regions are those of the fixed-order loop; warps of a persistent grid
 // take them one at a time from a counter, so that regions with long lists
@@ -393,6 +513,10 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
     int2 *dst = a.vadjR;
     const int32_t *nsrc = r <= 2 ? a.vnbrE : a.vnbrR;  // graphs
     int32_t *ndst = a.vnbrR;
+    if (r == 1) {  // uniform: round 1 is a flat scan of every list (k_rpropose builds the kept list)
+        flat_round1<kPairs>(a, reinterpret_cast<uint32_t *>(&s_tile[threadIdx.x >> 5]));
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     unsigned long long scanned = 0, nlive = 0;
@@ -430,20 +554,8 @@ __global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
             const uint32_t L = act && !lng ? (uint32_t)rec.w : 0u;
             unsigned long long best = 0;
             uint32_t live = 0;
-            uint32_t Lmax = 0;
-            if (kPairs && r == 1) {
-                Lmax = L;
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) Lmax = max(Lmax, __shfl_xor_sync(kFull, Lmax, d));
-            }
-            if (kPairs && r == 1 && Lmax <= kSeqMax) {  // warp-uniform
-                if (L) best = first_round_max(a.vadjE, (int64_t)(uint32_t)rec.z, L, a.noise_s0, a.noise_scale);
-                live = L;
-                scanned += L;
-            } else {
-                scan_tile<kPairs>(a, r, src, dst, nsrc, ndst, L, (uint32_t)rec.z, s_tile[threadIdx.x >> 5], best,
-                                  live, scanned);
-            }
+            scan_tile<kPairs>(a, r, src, dst, nsrc, ndst, L, (uint32_t)rec.z, s_tile[threadIdx.x >> 5], best, live,
+                              scanned);
             // the vertex's best key goes to k_rpropose, which makes every
             // proposal of the round (a dependent chain of random reads that
             // would otherwise sit in this scan's critical path)
@@ -555,13 +667,52 @@ __global__ void __launch_bounds__(kT) k_rpropose(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
     const int r = st->round, par = st->parity;
-    const int32_t *out = par ? a.list0 : a.list1;
-    const uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
+    int32_t *out = par ? a.list0 : a.list1;
+    uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
     unsigned long long props = 0;
+    if (r == 1) {  // uniform: the flat scan left every vertex's largest key; keep those with a list
+        int32_t *keep_out = out;
+        for (uint64_t g = warp; g < a.nregions; g += nwarps) {
+            const uint64_t base = g * a.region;
+            const int64_t left = a.n - (int64_t)base;
+            const uint32_t c = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.region ? left : (int64_t)a.region);
+            uint32_t won = 0, kept = 0;
+            for (uint32_t i0 = 0; i0 < c; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                bool w = false, keep = false;
+                int32_t nb = -1;
+                const int32_t v = (int32_t)(base + i);
+                if (i < c) {
+                    const unsigned long long best = a.rbest[v];
+                    if (best != 0) {
+                        const int32_t e = edge_of_key(best);  // T[v], input id
+                        reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(e, 0);
+                        w = propose(a, r, e);
+                        if (w) nb = __ldg(a.jof + e);
+                        keep = true;
+                        ++props;
+                    }
+                }
+                const unsigned km = __ballot_sync(kFull, keep);
+                if (keep) keep_out[base + kept + __popc(km & lt)] = v;
+                kept += __popc(km);
+                const unsigned wm = __ballot_sync(kFull, w);
+                if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
+                won += __popc(wm);
+            }
+            if (lane == 0) {
+                cnt_out[g] = kept;
+                if (kept) atomicAdd(&st->cnt[par ^ 1], kept);
+            }
+            if (won) flush_winners(a, base, won);
+        }
+        block_add_u64(props, s_red, &st->proposals);
+        return;
+    }
     for (uint64_t g = warp; g < a.nregions; g += nwarps) {
         const uint32_t c = cnt_out[g];
         const uint64_t base = g * a.region;
@@ -602,6 +753,21 @@ __global__ void __launch_bounds__(kT) k_rpropose(RoundArgs a) {
 __global__ void __launch_bounds__(kT) k_pair_endpoints(const int2 *vpair, uint64_t kappa, int32_t *vnbrE) {
     for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += (uint64_t)gridDim.x * kT)
         vnbrE[i] = vpair[i].y;
+}
+
+// Round 1's flat scan: the vertex whose list holds entry c * kFlatW, for
+// every chunk c (the largest v with voff[v] <= c * kFlatW).
+__global__ void __launch_bounds__(kT) k_vchunk(const int64_t *voff, int64_t n, uint64_t nchunks, int32_t *vchunk) {
+    for (uint64_t c = blockIdx.x * (uint64_t)kT + threadIdx.x; c < nchunks; c += (uint64_t)gridDim.x * kT) {
+        const uint64_t p = c * kFlatW;
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if ((uint64_t)voff[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        vchunk[c] = (int32_t)lo;
+    }
 }
 
 // The proposal words' start value by input id: |e| in the upper half.
@@ -659,6 +825,8 @@ RoundArgs rand_args(const Handle *h) {
     a.S64 = h->S64;
     a.W64a = h->W64a;
     a.W64b = h->W64b;
+    a.vchunk = h->vchunk;
+    a.kappa = h->kappa;
     a.lq = h->lq;
     a.rbest = h->rbest;
     a.lq_cap = h->lq_cap;
@@ -740,12 +908,13 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
         (st = dalloc(&h->vadjR, h->kappa, s, "re-randomised vertex lists")) != HM_OK ||
         (st = dalloc(&h->jof, m, s, "inverse edge order")) != HM_OK ||
         (st = dalloc(&h->P2, m, s, "second proposal counters")) != HM_OK ||
-        (h->p16 && (st = dalloc(&h->S32, m, s, "edge sizes")) != HM_OK) ||
+        (h->p16 && !h->graph && (st = dalloc(&h->S32, m, s, "edge sizes")) != HM_OK) ||
         (!h->p16 && ((st = dalloc(&h->S64, m, s, "edge sizes")) != HM_OK ||
                      (st = dalloc(&h->W64a, m, s, "proposal counters")) != HM_OK ||
                      (st = dalloc(&h->W64b, m, s, "proposal counters")) != HM_OK)) ||
         (st = dalloc(&h->lq, h->lq_cap, s, "long-list queue")) != HM_OK ||
         (st = dalloc(&h->rbest, n, s, "largest keys of the round")) != HM_OK ||
+        (st = dalloc(&h->vchunk, (h->kappa + kFlatW - 1) / kFlatW + 1, s, "flat chunk vertices")) != HM_OK ||
         (h->graph && ((st = dalloc(&h->vnbrE, h->kappa, s, "list endpoints")) != HM_OK ||
                       (st = dalloc(&h->vnbrR, h->kappa, s, "re-randomised list endpoints")) != HM_OK))) {
         free_rand_buffers(h);
@@ -756,8 +925,12 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
     if (m) {
         k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
             h->order, h->vadj, h->weighted ? h->weights : nullptr, h->m, h->kappa, h->vadjE, h->vadjR, h->jof);
-        k_size_words<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->m, h->graph ? 1 : 0,
-                                                                    h->S32, h->S64);
+        if (!h->graph)  // graphs count in bytes and need no sizes
+            k_size_words<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->m, 0, h->S32,
+                                                                        h->S64);
+        const uint64_t nchunks = (h->kappa + kFlatW - 1) / kFlatW;
+        if (nchunks)
+            k_vchunk<<<grid_for(nchunks, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, h->n, nchunks, h->vchunk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             free_rand_buffers(h);
@@ -827,7 +1000,7 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
 
 void free_rand_buffers(Handle *h) {
     void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->rbest, h->vnbrE, h->vnbrR,
-                    h->S32, h->S64, h->W64a, h->W64b};
+                    h->S32, h->S64, h->W64a, h->W64b, h->vchunk};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, h->cap_stream);
     h->vrecR = nullptr;
@@ -841,6 +1014,7 @@ void free_rand_buffers(Handle *h) {
     h->S64 = nullptr;
     h->W64a = nullptr;
     h->W64b = nullptr;
+    h->vchunk = nullptr;
     h->vnbrE = nullptr;
     h->vnbrR = nullptr;
     if (h->exec_rand) cudaGraphExecDestroy(h->exec_rand);
