@@ -178,17 +178,50 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
     """Element bytes of this design per kernel kind, summed over rounds, from
     the per-round counters of hm_round_stats. p16: the fixed order's P
     counters are 16 bits wide (every edge has at most 65535 pins). pairs: a
-    graph in the fixed order (lists of {edge, other endpoint}, liveness from
-    the endpoints' matched flags, no kill step)."""
+    graph (fixed order: lists of {edge, other endpoint}, liveness from the
+    endpoints' matched flags, no kill step; re-randomised rounds: the same
+    edge rounds as a hypergraph, with two pins an edge)."""
     ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT, LIVE = range(9)
+    LEDGES = 10
     pc = 2 if p16 else 4  # bytes of one P counter
-    if random:  # flags, two counter buffers, mask; records, offsets; list copy
-        init = float(m * (1 + 4 + 4 + 1) + n * (16 + 16) + kappa * 8)
+    if random:  # flag, counter word read + write, mask; matched flag, two key slots,
+                # offset pair, first entry, record write
+        init = float(m * (1 + 4 + 4 + 1) + n * (1 + 8 + 8 + 16 + 4 + 16))
     elif pairs:  # mask, P copied from its initial copy; matched flags
         init = float(m * (1 + 2 * pc) + n)
     else:       # flag, mask, P copied from its initial copy (read + write)
         init = float(m * (1 + 1 + 2 * pc))
     b = {"init": init, "argmax": 0.0, "win": 0.0, "kill": 0.0, "round_end": 0.0}
+    if random:
+        for r, row in enumerate(stats):
+            row = row.astype(np.float64)
+            if r == 0:
+                # round 1, vertex-driven: every list entry; per vertex its offsets
+                # and largest key written; proposal = key read, record write,
+                # counter word read + write; kept = list write; winner = its id
+                b["argmax"] += (row[ADV] * 8 + n * (8 + 8) + row[PROP] * (8 + 8 + 4 + 4)
+                                + row[NEXT] * 4 + row[WIN] * 4)
+                if pairs:  # winner: order, mask; winner pin: pin, matched flag
+                    b["win"] += row[WIN] * (4 + 1 + 4) + row[WPIN] * (4 + 1)
+                else:      # winner: offset pair, order, mask; winner pin: pin, record
+                           # read + write; kill range: item write
+                    b["win"] += row[WIN] * (16 + 4 + 1 + 4) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 8
+                b["kill"] += row[ITEM] * 8 + row[KILL] * (8 + 1)  # killed entry: list entry + flag
+                continue
+            # an edge round: records in (round 2: every edge, hypergraphs read its
+            # live flag; later: the previous round's live edges), a tested pin
+            # (pin + matched flag), a live edge's record written and its pins'
+            # 8-byte offers; the win pass reads each live record, pin and slot,
+            # marks winners (mask) and their pins (flag), and clears the other
+            # slot buffer (8 n)
+            rec_in = m if r == 1 else float(stats[r - 1, LEDGES])
+            flag = m if (r == 1 and not pairs) else 0
+            tested = 0.0 if (r == 1 and not pairs) else row[ADV]
+            b["argmax"] += (rec_in * 16 + flag + tested * (4 + 1) + row[LEDGES] * 16
+                            + row[LIVE] * ((4 if tested == 0 else 0) + 8))
+            b["win"] += (row[LEDGES] * 16 + row[LIVE] * (4 + 8) + row[WIN] + row[WPIN]
+                         + (n * 8 if row[LIVE] > 0 else 0))
+        return b
     for r, row in enumerate(stats):
         row = row.astype(np.float64)
         if pairs:  # winner: order, mask; winner pin: pin, matched flag
@@ -196,15 +229,7 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
         else:  # winner: offset pair, order, mask; winner pin: pin, record read +
                # write; kill range: item write
             winb = row[WIN] * (16 + 4 + 1) + row[WPIN] * (4 + 16 + 8) + row[ITEM] * 8
-        if random:  # list + record; scanned entry = entry + flag; live entry = id/base
-                    # record + compacted write; proposal = largest key written and read
-                    # back, kept-list read, record read + write, counter word read +
-                    # write (its size rides in it), clear of the previous count; kept =
-                    # list write; winner = its relabelled id
-            b["argmax"] += (row[ACT] * ((4 if r else 0) + 16) + row[ADV] * (4 + 1)
-                            + row[LIVE] * (8 + 4) + row[PROP] * (8 + 8 + 4 + 16 + 8 + 8 + 4)
-                            + row[NEXT] * 4 + row[WIN] * 4)
-        elif pairs:
+        if pairs:
             if r == 0:  # first entry + its other endpoint + offset pair read, record write
                 b["argmax"] += row[ACT] * (4 + 4 + 16 + 16) + row[PROP] * 2 * pc + row[NEXT] * 4
             else:       # list + record + matched flag; skipped entry = pair + flag;
@@ -235,8 +260,8 @@ def method_argmax_bytes(stats: np.ndarray) -> float:
     active vertex 8 (entry 4, gathered priority-or-dead word 4). Units from
     hm_round_stats: the active vertices of round r (HM_STAT_NEXT) and the sum
     of their degrees (HM_STAT_DEG). The fixed order resumes each vertex at its
-    cursor, and the re-randomised rounds scan compacted lists, so the kernels
-    move fewer bytes than this count."""
+    cursor, and the re-randomised rounds from the second on touch only the
+    pins of live edges, so the kernels move fewer bytes than this count."""
     NEXT, DEG = 7, 9
     s = stats.astype(np.float64)
     return float(s[:, NEXT].sum() * 24 + s[:, DEG].sum() * 8)
@@ -303,8 +328,8 @@ TRAFFIC_ROWS = {
     ("win", False): ("k_win", "rounds.cu"),
     ("kill", False): ("k_kill", "rounds.cu"),
     ("init", True): ("k_rinit", "rrounds.cu"),
-    ("argmax", True): ("k_rargmax+k_rlong+k_rpropose", "rrounds.cu"),
-    ("win", True): ("k_win", "rounds.cu"),
+    ("argmax", True): ("k_rflat+k_rpropose+k_epush", "rrounds.cu"),
+    ("win", True): ("k_win+k_ewin", "rrounds.cu"),
     ("kill", True): ("k_kill", "rounds.cu"),
 }
 TRAFFIC_FILE = os.path.join("profiles", "traffic.json")
@@ -755,7 +780,7 @@ def run_ours(args, world, rank, local):
     stats = mt.round_stats()
     create_ms = mt.create_ms()
     max_size = int(np.diff(h.eoff).max()) if h.m else 0
-    pairs = not rnd_mode and h.m > 0 and max_size == 2 and h.kappa == 2 * h.m  # a graph
+    pairs = h.m > 0 and max_size == 2 and h.kappa == 2 * h.m  # a graph
     kb = kernel_bytes(stats, h.n, h.m, h.kappa, rnd_mode, p16=max_size <= 0xFFFF, pairs=pairs)
     dom = max(("argmax", "win", "kill"), key=lambda k: prof[k][0])
     assert all(isinstance(prof[k], tuple) for k in hm.KERNELS)
@@ -784,7 +809,7 @@ def run_ours(args, world, rank, local):
     kills = float(stats[:, hm.STAT_COLUMNS.index("kills")].sum())
     rar = random_access_roofline(stats, prof, ra, rnd_mode)
     loop_ms = sum(prof[k][0] for k in hm.KERNELS)
-    rounds_run = int(prof["win"][1])  # one win launch a round (the argmax step is three kernels when re-randomised)
+    rounds_run = int(prof["win"][1])  # one win launch a round
     # the whole match: the method's bytes of steps a1-a4 (the plain
     # formulation), this design's element bytes, and the DRAM bytes ncu
     # counted (committed rows), each over the timed match
@@ -809,8 +834,9 @@ def run_ours(args, world, rank, local):
                  "dram__bytes per launch (profiles/traffic.json) times launches"),
     }
     # init + three kernels per round (argmax, win, kill with the round end);
-    # five in the re-randomised rounds (the argmax step is three kernels there)
-    launches = 1 + (5 if rnd_mode else 3) * rounds_run
+    # re-randomised: four in round 1 (scan, proposals, win, kill), two in
+    # each later round (offers, win test with the round end)
+    launches = 1 + ((4 + 2 * (rounds_run - 1)) if rnd_mode else 3 * rounds_run)
 
     out = {}
     if rank == 0:

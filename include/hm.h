@@ -143,11 +143,10 @@ hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
  * amplitude). The 1/d bound of Lemma 1 holds for the cardinality of the
  * matching (unweighted input) in this mode; with weights plus noise the
  * matching is locally maximal for the noisy priorities, not for w.
- * The first match with amplitude > 0 allocates 16*kappa + 24*n + 12*m bytes
- * more on the device (20*m more when some edge has more than 65535 pins;
- * 24*kappa + 24*n + 8*m for a graph, every edge with two pins) plus 8 bytes
- * per 2048 pins and 4 bytes per 1024 pins (owned by the handle until
- * hm_destroy).
+ * The first match with amplitude > 0 allocates 8*kappa + 33*n + 60*m bytes
+ * more on the device (12*m more when some edge has more than 65535 pins;
+ * 8*kappa + 32*n + 56*m for a graph, every edge with two pins) plus 4 bytes
+ * per 1024 pins and a few KB (owned by the handle until hm_destroy).
  * hm_autotune tunes the fixed-order loop and leaves the amplitude set.
  * Errors: HM_EINVAL (NULL handle, amplitude negative, NaN or infinite).
  */
@@ -203,7 +202,13 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
 /*
  * hm_round_stats - per-round counters of the last match (waits for it).
  * For round r (0-based, r < min(rounds_cap, 4096)) row r of HOST
- * int64[max_rounds][HM_STATS_COLS] receives:
+ * int64[max_rounds][HM_STATS_COLS] receives the counters below. In the
+ * re-randomised rounds (hm_set_noise) rounds from the second on are
+ * edge-driven: there ADVANCE counts the pins tested, PROPOSALS and LIVE the
+ * keys offered (the live pins), KILLS the pins of the edges found dead
+ * (killed by the previous round's winners), ITEMS is 0, and ACTIVE, NEXT
+ * (the vertices offered a key: those active at the round's start) and DEG
+ * are counted by hm_profile_match only (0 after hm_match).
  */
 #define HM_STAT_ACTIVE    0  /* vertices visited by the argmax step */
 #define HM_STAT_ADVANCE   1  /* adjacency entries skipped by the argmax step (fixed
@@ -216,8 +221,8 @@ hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream
                                 liveness from its endpoints and have no kill step) */
 #define HM_STAT_ITEMS     6  /* kill ranges (one per newly matched vertex) */
 #define HM_STAT_NEXT      7  /* vertices kept for the next round */
-#define HM_STAT_LIVE      8  /* re-randomised rounds: live entries the argmax scan
-                                found; 0 in the fixed order */
+#define HM_STAT_LIVE      8  /* re-randomised rounds: live list entries (the live
+                                pins) of the round; 0 in the fixed order */
 #define HM_STAT_DEG       9  /* after hm_profile_match only (a counting kernel it
                                 runs between its timed kernels): sum of the degrees
                                 of the vertices kept (HM_STAT_NEXT: the unmatched

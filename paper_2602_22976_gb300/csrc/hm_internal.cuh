@@ -85,7 +85,6 @@ struct DevState {
     uint32_t cnt[2];      // sizes of list0 / list1
     uint32_t nwin;        // winners of this round
     uint32_t kdone;       // blocks of the kill step that have finished
-    uint32_t rgrab;       // re-randomised rounds: next region to hand out this round
     int32_t status;       // HM_OK, HM_ETIMEOUT, HM_EINVAL (inconsistent input)
     int32_t rounds_done;  // rounds that started with a live edge
     int32_t finished;     // 1 once the loop has stopped
@@ -94,12 +93,12 @@ struct DevState {
     unsigned long long kills;
     unsigned long long winpins;
     unsigned long long proposals;
-    unsigned long long lpack;      // re-randomised rounds: (long lists << 32) | their chunks
-    unsigned long long live;       // re-randomised rounds: live entries found by the scan
+    unsigned long long live;       // re-randomised rounds: live entries (pins of live edges) of the round
     unsigned long long sdeg;       // profiled rounds: degrees of the vertices kept
     unsigned long long kpack;      // kill ranges of the round: (entries << 32) | items
-    unsigned long long ledges;     // profiled rounds: edges live at the start of the round
-    unsigned long long lpins;      // profiled rounds: their pins
+    unsigned long long ledges;     // edges live at the start of the round (profiled rounds; every
+                                   // re-randomised round from the second on)
+    unsigned long long lpins;      // their pins
 };
 
 // One kill range: list entries [begin, begin + length) where length is the
@@ -152,22 +151,48 @@ struct RoundArgs {
     float noise_scale;          // amplitude * 2^-24
     uint64_t noise_s0;          // SplitMix64 start state of the priority stream
     const int2 *vadjE;          // vertex lists as {input edge id, bits(base priority)}
-    int2 *vadjR;                // working copy, compacted every round
-    const int32_t *vnbrE;       // graphs: other endpoint of every vadjE entry
-    int32_t *vnbrR;             // graphs: the same for vadjR, compacted with it
     const int32_t *jof;         // input id -> j
-    uint32_t *P2;               // second proposal counter buffer
+    uint32_t *P2;               // round 1's proposal counters (32-bit words)
     int t_input;                // T[v] holds input edge ids (re-randomised rounds), not j
     int w64;                    // proposal words are 64-bit (some edge has more than 65535 pins)
     const uint32_t *S32;        // |e| << 16 by input id: the proposal words' start value
     const unsigned long long *S64;  // |e| << 32 (w64)
-    unsigned long long *W64a, *W64b;  // 64-bit proposal words by round parity (w64)
+    unsigned long long *W64;    // round 1's 64-bit proposal words (w64)
     const int32_t *vchunk;      // round 1: the vertex owning list entry c * kFlatW, per flat chunk c
     uint64_t kappa;             // list entries
-    int2 *lq;                   // long lists of the round: {vertex, first chunk}
-    unsigned long long *rbest;  // every active vertex's largest key of the round
-    uint32_t lq_cap;            // capacity of lq
+    unsigned long long *rbest;  // largest key offered to each vertex in odd rounds
+    unsigned long long *rbest2; // the same in even rounds (rounds >= 2)
+    const int4 *erec;           // every edge in j order: {input id, bits(base priority), first pin, size}
+    int4 *elist[2];             // rounds >= 2: the live edges of round r (records as erec) at index r & 1,
+                                // in eregions regions of eregion records (erec: the same regions, full)
+    uint32_t *ecnt;             // [2][eregions]: live records in each region of elist[0] / elist[1]
+    uint32_t eregions, eregion;
+    int erounds;                // re-randomised rounds: rounds >= 2 are edge rounds (round 1 ends accordingly)
+    int profiled;               // the per-kernel replay: edge rounds record their live edges and pins
 };
+
+// Stats row of round r (rounds beyond kStatRounds are not recorded).
+__device__ inline void write_stats_row(const RoundArgs &a, int r, int64_t active, uint32_t nw, uint32_t next,
+                                unsigned long long adv, unsigned long long props, unsigned long long winpins,
+                                unsigned long long kills, uint32_t items, unsigned long long live,
+                                unsigned long long sdeg, unsigned long long ledges, unsigned long long lpins) {
+    if (r >= 1 && r - 1 < kStatRounds) {
+        int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
+        row[HM_STAT_ACTIVE] = active;
+        row[HM_STAT_ADVANCE] = (int64_t)adv;
+        row[HM_STAT_PROPOSALS] = (int64_t)props;
+        row[HM_STAT_WINNERS] = nw;
+        row[HM_STAT_WINPINS] = (int64_t)winpins;
+        row[HM_STAT_KILLS] = (int64_t)kills;
+        row[HM_STAT_ITEMS] = items;
+        row[HM_STAT_NEXT] = next;
+        row[HM_STAT_LIVE] = (int64_t)live;
+        row[HM_STAT_DEG] = (int64_t)sdeg;
+        row[HM_STAT_LEDGES] = (int64_t)ledges;
+        row[HM_STAT_LPINS] = (int64_t)lpins;
+    }
+}
+
 
 struct Handle {
     int device = 0;
@@ -207,21 +232,22 @@ struct Handle {
     float noise = 0.f;          // 0: fixed order; > 0: amplitude of the per-round noise
     float graph_noise = 0.f;    // amplitude exec_rand was built with
     bool last_random = false;   // the last match ran re-randomised rounds
-    int4 *vrecR = nullptr;      // {T[v], 0, list start, live list length}
+    int4 *vrecR = nullptr;      // round 1: {T[v], 0, list start, list length}
     int2 *vadjE = nullptr;      // vertex lists as {input edge id, bits(base priority)} (built once)
-    int2 *vadjR = nullptr;      // working copy: short lists rewritten every match, long ones never
-    int32_t *vnbrE = nullptr;   // graphs: other endpoint of every list entry (liveness from vmatch)
-    int32_t *vnbrR = nullptr;   // graphs: working copy, compacted with vadjR
+    int4 *erec = nullptr;       // edge records in j order (built once)
+    int4 *elist0 = nullptr, *elist1 = nullptr;  // live edge lists of the edge rounds
+    uint32_t *ecnt = nullptr;                   // their region lengths
+    uint32_t eregions = 0, eregion = 0;
+    unsigned long long *rbest2 = nullptr;       // even rounds' largest keys per vertex
+    uint8_t *rmatch = nullptr;  // hypergraphs: matched flag per vertex in the edge rounds
     int32_t *jof = nullptr;
     uint32_t *P2 = nullptr;
     uint32_t *S32 = nullptr;              // |e| << 16 by input id (every edge <= 65535 pins)
     unsigned long long *S64 = nullptr;    // |e| << 32 by input id (otherwise)
-    unsigned long long *W64a = nullptr, *W64b = nullptr;
+    unsigned long long *W64 = nullptr;    // 64-bit proposal words (otherwise)
     int32_t *vchunk = nullptr;            // round 1's flat scan: vertex of every chunk's first entry
-    int2 *lq = nullptr;
-    unsigned long long *rbest = nullptr;  // re-randomised rounds: largest key of the round per vertex
-    uint32_t lq_cap = 0;
-    unsigned rargmax_grid = 0, rlong_grid = 0, rpropose_grid = 0;
+    unsigned long long *rbest = nullptr;  // re-randomised rounds: largest key offered per vertex (odd rounds)
+    unsigned rflat_grid = 0, rpropose_grid = 0, epush_grid = 0, ewin_grid = 0;
     cudaGraphExec_t exec_rand = nullptr;
     int64_t graph_cap_rand = -1;
     LaunchConfig graph_cfg_rand;
@@ -349,6 +375,8 @@ hm_status launch_match_graph_rand(Handle *h, cudaStream_t s);
 hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *launches, double *round_ms,
                              int32_t max_rounds);
 void free_rand_buffers(Handle *h);
+// The per-vertex state after the last re-randomised match (hm_vertex_state).
+cudaError_t launch_rand_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s);
 
 // SplitMix64 (Steele, Lea, Flood 2014): output number k (k >= 1) of the
 // generator whose state starts at s0. The first output for a seed is

@@ -93,13 +93,12 @@ __global__ void __launch_bounds__(kT) k_init(RoundArgs a) {
         st->cnt[0] = st->cnt[1] = 0;
         st->nwin = 0;
         st->kdone = 0;
-        st->rgrab = 0;
         st->status = HM_OK;
         st->rounds_done = 0;
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = st->live = st->kpack = st->sdeg = 0;
+        st->live = st->kpack = st->sdeg = 0;
         st->ledges = st->lpins = 0;
     }
 }
@@ -587,21 +586,7 @@ __device__ int finish_round(const RoundArgs &a, DevState *st, int r, int64_t act
                             unsigned long long winpins, unsigned long long kills, uint32_t items,
                             unsigned long long live, unsigned long long sdeg, unsigned long long ledges,
                             unsigned long long lpins) {
-    if (r - 1 < kStatRounds) {
-        int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
-        row[HM_STAT_ACTIVE] = active;
-        row[HM_STAT_ADVANCE] = (int64_t)adv;
-        row[HM_STAT_PROPOSALS] = (int64_t)props;
-        row[HM_STAT_WINNERS] = nw;
-        row[HM_STAT_WINPINS] = (int64_t)winpins;
-        row[HM_STAT_KILLS] = (int64_t)kills;
-        row[HM_STAT_ITEMS] = items;
-        row[HM_STAT_NEXT] = next;
-        row[HM_STAT_LIVE] = (int64_t)live;
-        row[HM_STAT_DEG] = (int64_t)sdeg;
-        row[HM_STAT_LEDGES] = (int64_t)ledges;
-        row[HM_STAT_LPINS] = (int64_t)lpins;
-    }
+    write_stats_row(a, r, active, nw, next, adv, props, winpins, kills, items, live, sdeg, ledges, lpins);
     int cont = 0;
     if (st->fault) {
         st->status = HM_ECUDA;
@@ -630,13 +615,28 @@ __device__ void round_end(const RoundArgs &a) {
     const uint32_t nw = st->nwin, next = st->cnt[par ^ 1];
     const int64_t active = r == 1 ? a.n : (int64_t)st->cnt[par];
     const unsigned long long kp = st->kpack;
-    const int cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, kp >> 32,
-                                  (uint32_t)kp, st->live, st->sdeg, st->ledges, st->lpins);
+    int cont;
+    if (a.erounds) {
+        // re-randomised round 1, followed by edge rounds: record it; the
+        // next round's first pass finds whether any edge is still live and
+        // applies the round cap (no winner: no edge was live at all)
+        write_stats_row(a, r, active, nw, next, st->adv, st->proposals, st->winpins, kp >> 32, (uint32_t)kp,
+                        st->live, st->sdeg, st->ledges, st->lpins);
+        cont = 0;
+        if (st->fault) st->status = HM_ECUDA;
+        else if (nw == 0) st->rounds_done = 0;
+        else {
+            st->rounds_done = 1;
+            cont = 1;
+        }
+    } else {
+        cont = finish_round(a, st, r, active, nw, next, st->adv, st->proposals, st->winpins, kp >> 32,
+                            (uint32_t)kp, st->live, st->sdeg, st->ledges, st->lpins);
+    }
     st->nwin = 0;
     st->kdone = 0;
-    st->rgrab = 0;
     st->adv = st->kills = st->winpins = st->proposals = 0;
-    st->lpack = st->live = st->kpack = st->sdeg = 0;
+    st->live = st->kpack = st->sdeg = 0;
     st->ledges = st->lpins = 0;
     if (cont) {
         st->round = r + 1;
@@ -761,15 +761,15 @@ __global__ void __launch_bounds__(kT) k_kill(RoundArgs a) {
     }
 }
 
-// vmatch (graphs in the fixed order, else null): the matched flags, which
-// there stand in for T[v] = kCurMatched.
-// order null: T[v] holds input ids already (the re-randomised rounds).
+// The per-vertex state after a fixed-order match. vmatch (graphs, else
+// null): the matched flags, which there stand in for T[v] = kCurMatched;
+// order maps T[v] (a relabelled id) to the input id.
 __global__ void k_vertex_state(const int4 *vrec, const uint8_t *vmatch, const int32_t *order, int64_t n,
                                int32_t *out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = vmatch && vmatch[v] ? kCurMatched : vrec[v].x;
-        out[v] = j >= 0 ? (order ? order[j] : j) : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
+        out[v] = j >= 0 ? order[j] : (j == kCurMatched ? HM_VERTEX_MATCHED : HM_VERTEX_NONE);
     }
 }
 
@@ -1182,10 +1182,11 @@ hm_status autotune(Handle *h, cudaStream_t s, LaunchConfig *best, double *best_m
 }
 
 cudaError_t launch_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
-    const int4 *vrec = h->last_random ? h->vrecR : h->vrec;
+    if (h->last_random) return launch_rand_vertex_state(h, out_dev, s);
+    const int4 *vrec = h->vrec;
     const uint8_t *vmatch = h->vmatch;  // graphs (both orders): the matched flags
-    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(
-        vrec, vmatch, h->last_random ? nullptr : h->order, h->n, out_dev);
+    k_vertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(vrec, vmatch, h->order, h->n,
+                                                                               out_dev);
     return cudaGetLastError();
 }
 

@@ -8,50 +8,47 @@
 // the seed, times 2^-24. Nothing random is stored: every key is recomputed
 // from (seed, r, e) where it is needed.
 //
-// With priorities that change every round there is no fixed list order for
-// a cursor to walk. Every round each active vertex scans its live list,
-// takes the largest key among the live entries (Alg. 3's argmax), and
-// compacts it, so an entry is read at most once after its edge died. List
-// entries carry what the key needs, {input edge id e, bits(base_e)}, so
-// round 1 streams the lists with no random read at all (every edge is live
-// then); later rounds add one 1-byte live-flag read per entry, from an
-// array indexed by input id (m bytes, L2-resident). Round 1 reads the
-// immutable lists (vadjE) and writes nothing (it keeps every entry); round 2
-// reads vadjE and writes the compacted lists to the working copy (vadjR);
-// later rounds compact vadjR in place. Lists are scheduled by length:
-//   - at most kLong entries: the 32 vertices of a warp tile are scanned as
-//     one concatenated sequence, each lane taking kE consecutive entries of
-//     a batch (scan_tile: per-list maxima folded in shared memory, one warp
-//     scan per batch for the compaction offsets), so short and medium lists
-//     keep every lane busy;
-//   - longer lists: queued with their chunk count (one 64-bit atomic hands
-//     out the queue slot and the first chunk); k_rlong scans the chunks of
-//     kChunk entries with one warp each and combines them per list with a
-//     64-bit atomicMax. Long lists are not compacted: they are scanned from vadjE,
-//     and their part of vadjR (read by the kill step) is copied once when
-//     the handle first runs this mode and never written.
-// Proposals use the P counter of Alg. 1 counted up and double-buffered by
-// round parity, indexed by input edge id and packed with the edge's size
-// (propose): a vertex adds 1 to P_r[T[v]] and learns from the same atomic
-// whether the count reached |e| (the edge wins); it clears the count it
-// added in the previous round in the other buffer, which the next round
-// reuses. Every vertex that proposed a still-live edge is active in the
-// next round and clears it; stale counts are left only on dead edges, which
-// nobody proposes again. T[v] holds the input id; the winner list holds
-// relabelled ids j (looked up for the winners only). The scans leave each
-// vertex's largest key of the round in rbest; k_rpropose then makes all
-// proposals of the round, one vertex per thread, so a proposal's random
-// access is not on the scans' critical path.
-// The win kernel and the kill kernel (which ends the round) of rounds.cu
-// run on this handle's re-randomised vertex records and lists: the cursor
-// field stays 0, so the kill range of a matched vertex is its whole
-// (compacted) list, and the kill step (reading every second word: the edge
-// ids of the pairs; from vadjE in round 1) clears the flags of the input ids
-// there. Graphs (every edge has two pins) need no kill: each list entry
-// also has its edge's other endpoint (vnbrE, compacted into vnbrR with the
-// pairs), an entry is live while that endpoint is unmatched, the win step
-// only sets the matched flags of the winners' endpoints, and a vertex whose
-// own flag is set drops out.
+// A round is Alg. 1's three steps with these keys: every vertex takes the
+// largest key among its live edges (T[v]), an edge chosen by all of its
+// pins joins the matching, and edges with a matched pin die. Two
+// formulations compute it, each where its cost is lowest.
+//
+// Round 1 (every edge live) is vertex-driven. The vertex lists, stored as
+// {input edge id e, bits(base_e)} pairs (vadjE), are read as one flat array
+// (flat_round1) with no random read at all; each vertex's largest key goes
+// to rbest. k_rpropose then makes every proposal (the P counter of Alg. 1,
+// counted up by input id and packed with the edge's size, so one atomic
+// tells whether the count reached |e|), and the win and kill kernels of
+// rounds.cu finish the round: the winners' vertices are marked, and every
+// entry of their lists is cleared in the m-byte live-flag array.
+//
+// Rounds 2 on are edge-driven, on a list of the edges still live (records
+// {e, bits(base_e), first pin, |e|}, in j order for round 2: erec). After
+// round 1 most list entries belong to dead edges (on the power-law bench
+// instance 3.7e7 of the 1.78e8 entries of the vertices still active), so a
+// vertex-driven round would pay one random live-flag read per dead entry;
+// here a round touches only the pins of the edges live in the round before:
+//   k_epush: the previous round's live list (round 2: every edge) is
+//     filtered - an edge is live while none of its pins is matched (in
+//     round 2 of a hypergraph: while the live flag that round 1's kill step
+//     maintained is set) - and compacted into this round's list, and every
+//     live edge offers key_r(e) to each pin with a 64-bit atomicMax on the
+//     vertex's slot of this round's buffer: the slot ends as the key of
+//     T[v] (step 1).
+//   k_ewin: an edge whose key is in the slot of every pin won (step 2): it
+//     joins the matching and its pins are marked matched; the deaths this
+//     causes are found by the next round's filter (step 3). It also clears
+//     the other buffer whole (a streaming pass: cheaper than a random store
+//     per live pin), so that the next round starts from zero slots and a
+//     nonzero slot after a round means the vertex was offered a key in it;
+//     its last block ends the round.
+// Small edges (at most kSmall pins) are handled by one lane, which keeps
+// their pins in registers between the test and the offer; larger ones by
+// the whole warp, 32 pins at a time. The lists are split into fixed regions
+// (those of erec: eregion consecutive records each), a warp owns a region
+// at a time, and a region's live records are compacted to the front of the
+// same region of the next list with ballots: no counter shared by the whole
+// GPU (one such atomic per 32 records serialised the round on a graph).
 #include "hm_internal.cuh"
 
 #include <algorithm>
@@ -62,23 +59,12 @@ namespace {
 
 constexpr int kT = 256;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint32_t kLong = 2048;   // lists longer than this are scanned in chunks
-constexpr uint32_t kChunk = 2048;  // entries per chunk of a long list
+constexpr int kSmall = 8;  // edges with at most this many pins are handled by one lane
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
     return r;
-}
-
-__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
-    }
-    return x;
 }
 
 __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned long long *s_red,
@@ -121,38 +107,27 @@ __device__ __forceinline__ int32_t edge_of_key(unsigned long long k) {
     return (int32_t)(0xFFFFFFFFu - (uint32_t)k);
 }
 
-// The P counter of round r for input edge e, packed with the edge's size:
-// word = (|e| << H) | count, H = 16 when no edge has more than 65535 pins
-// (two 32-bit buffers), else H = 32 (two 64-bit buffers). A proposal adds 1
-// and gets the size back with the old count from the same atomic, so no
-// other read is needed to see whether it completed the edge; the clear of
-// the previous round's count keeps the size half. The buffers start each
+// Round 1's P counter for input edge e, packed with the edge's size: word
+// = (|e| << H) | count, H = 16 when no edge has more than 65535 pins (a
+// 32-bit word), else H = 32 (a 64-bit word). A proposal adds 1 and gets
+// the size back with the old count from the same atomic, so no other read
+// is needed to see whether it completed the edge. The words start each
 // match as copies of the sizes (k_rinit). A graph's edges all have two
 // pins: its counts are 8-bit, four to a 32-bit word, with no size beside
 // them (the count an edge reaches is at most 2), so the counters of m edges
 // take m bytes and stay in L2.
-__device__ __forceinline__ bool propose(const RoundArgs &a, int r, int32_t e) {
-    if (a.pairs) {  // graphs: every edge has two pins; four 8-bit counts a word, no size needed
-        uint32_t *W = (r & 1) ? a.P2 : a.P;
+__device__ __forceinline__ bool propose(const RoundArgs &a, int32_t e) {
+    if (a.pairs) {
         const int sh = (e & 3) * 8;
-        const uint32_t old = atomicAdd(W + (e >> 2), 1u << sh);
+        const uint32_t old = atomicAdd(a.P2 + (e >> 2), 1u << sh);
         return ((old >> sh) & 0xFFu) == 1u;
     }
     if (a.w64) {
-        unsigned long long *W = (r & 1) ? a.W64b : a.W64a;
-        const unsigned long long old = atomicAdd(W + e, 1ull);
+        const unsigned long long old = atomicAdd(a.W64 + e, 1ull);
         return (old & 0xFFFFFFFFull) + 1ull == (old >> 32);
     }
-    uint32_t *W = (r & 1) ? a.P2 : a.P;
-    const uint32_t old = atomicAdd(W + e, 1u);
+    const uint32_t old = atomicAdd(a.P2 + e, 1u);
     return (old & 0xFFFFu) + 1u == (old >> 16);
-}
-
-// Clears the count a vertex added to edge e in round r - 1 (its T then).
-__device__ __forceinline__ void clear_previous(const RoundArgs &a, int r, int32_t e) {
-    if (a.pairs) atomicAnd(((r & 1) ? a.P : a.P2) + (e >> 2), ~(0xFFu << ((e & 3) * 8)));
-    else if (a.w64) atomicAnd(((r & 1) ? a.W64a : a.W64b) + e, 0xFFFFFFFF00000000ull);
-    else atomicAnd(((r & 1) ? a.P : a.P2) + e, 0xFFFF0000u);
 }
 
 __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
@@ -161,24 +136,18 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         if (i < a.m) {
             a.alive[i] = 1;
             if (a.pairs) {  // four 8-bit counts a word
-                if (i < (a.m + 3) / 4) {
-                    a.P[i] = 0;
-                    a.P2[i] = 0;
-                }
+                if (i < (a.m + 3) / 4) a.P2[i] = 0;
             } else if (a.w64) {
-                const unsigned long long z = __ldg(a.S64 + i);
-                a.W64a[i] = z;
-                a.W64b[i] = z;
+                a.W64[i] = __ldg(a.S64 + i);
             } else {
-                const uint32_t z = __ldg(a.S32 + i);
-                a.P[i] = z;
-                a.P2[i] = z;
+                a.P2[i] = __ldg(a.S32 + i);
             }
             a.inM[i] = 0;
         }
         if (i < a.n) {
-            if (a.pairs) a.vmatch[i] = 0;
-            a.rbest[i] = 0;  // round 1 folds list pieces into it with atomicMax
+            a.vmatch[i] = 0;
+            a.rbest[i] = 0;   // round 1 folds list pieces into it with atomicMax
+            a.rbest2[i] = 0;  // round 2 offers its keys into it
             const int64_t b = a.voff[i], e = a.voff[i + 1];
             a.vrec[i] = make_int4(a.firstj[i], 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
         }
@@ -190,28 +159,20 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
         st->cnt[0] = st->cnt[1] = 0;
         st->nwin = 0;
         st->kdone = 0;
-        st->rgrab = 0;
         st->status = HM_OK;
         st->rounds_done = 0;
         st->finished = 0;
         st->fault = 0;
         st->adv = st->kills = st->winpins = st->proposals = 0;
-        st->lpack = st->live = st->kpack = st->sdeg = 0;
+        st->live = st->kpack = st->sdeg = 0;
         st->ledges = st->lpins = 0;
     }
 }
 
-// Adds a warp's counter to *dst with one atomic.
-__device__ __forceinline__ void warp_add_u64(unsigned long long x, unsigned long long *dst) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(dst, x);
-}
-
 // Appends a region's staged winners to the round's list with one atomic
 // (one counter word for the whole GPU: an atomic per winning step would
-// serialise on it). Kept out of line: inlined into k_rargmax it changed the
-// code of the scan loop and cost 0.3-0.5 ms in the scan-heavy rounds.
+// serialise on it). Kept out of line: inlined into the earlier scan
+// kernel it changed the code of its main loop and cost 0.3-0.5 ms.
 __device__ __noinline__ void flush_winners(const RoundArgs &a, uint64_t base, uint32_t won) {
     const int lane = threadIdx.x & 31;
     uint32_t wb = 0;
@@ -225,156 +186,10 @@ __device__ __noinline__ void flush_winners(const RoundArgs &a, uint64_t base, ui
     }
 }
 
-constexpr int kE = 4;  // consecutive entries a lane takes per batch of the tile scan
-constexpr int kFlatC = 32;              // round 1: consecutive entries a lane takes per chunk
+
+constexpr int kFlatC = 32;                // round 1: consecutive entries a lane takes per chunk
 constexpr uint64_t kFlatW = 32 * kFlatC;  // round 1: entries per warp chunk
-constexpr int kFlatSpan = 192;          // round 1: a chunk's vertex offsets staged in shared memory up to this many
-
-// Per-warp tile state of the scan in shared memory: for each lane's vertex
-// (its owner index) the start and end of its list in the tile's
-// concatenated sequence, the list's first entry in memory, the running
-// maximum key and live count, and the tile's live count before the list
-// (compaction offsets).
-struct TileSmem {
-    uint32_t pre[32], end[32], base[32], gst[32], live[32];
-    unsigned long long best[32];
-};
-// round 1 stages up to kFlatSpan vertex offsets in a warp's TileSmem
-static_assert(kFlatSpan * sizeof(uint32_t) <= sizeof(TileSmem), "the staged offsets must fit a warp's tile state");
-
-// The short and medium lists of a tile of 32 vertices (L = list length of
-// this lane's vertex, 0 when it takes no part; lb = its first entry), read
-// as one concatenated sequence in batches of 32 * kE entries: lane l takes
-// the kE consecutive positions from batch start + l * kE, finds the list
-// holding its first one by a binary search over the lists' starts, and
-// walks on (a run rarely crosses more than one list end). Each lane keeps
-// the maximum key and live count of every list piece in its run and folds
-// them into the list's shared entries with one atomic per piece. From round
-// 2 on the live entries are compacted: a warp scan of the lanes' live counts
-// gives every entry its place among the tile's live entries, and the live
-// count at each list's start (recorded by the lane holding that start)
-// turns it into the place in the list's own compacted copy. All reads of a
-// batch precede its writes (__syncwarp), and compacted entries land at or
-// before the positions they were read from, so compaction in place is safe.
-// Returns the list's maximum key (0: nothing live) and live count.
-template <bool kPairs>
-__device__ __forceinline__ void scan_tile(const RoundArgs &a, int r, const int2 *src, int2 *dst,
-                                          const int32_t *nsrc, int32_t *ndst, uint32_t L, uint32_t lb,
-                                          TileSmem &sm, unsigned long long &best, uint32_t &live,
-                                          unsigned long long &scanned) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t inc = warp_inclusive_scan(L);
-    const uint32_t total = __shfl_sync(kFull, inc, 31);
-    best = 0;
-    live = 0;
-    if (total == 0) return;  // warp-uniform
-    sm.pre[lane] = inc - L;
-    sm.end[lane] = inc;
-    sm.base[lane] = lb;
-    sm.best[lane] = 0;
-    sm.live[lane] = 0;
-    __syncwarp();
-    uint32_t gbase = 0;  // live entries of the tile before this batch
-    const uint64_t cr = round_counter_base(a.noise_s0, r);
-    for (uint32_t s0 = 0; s0 < total; s0 += 32 * kE) {
-        const uint32_t p0 = s0 + (uint32_t)lane * kE;
-        // the list holding p0: the largest x with pre[x] <= p0 (a non-empty
-        // list whenever p0 < total)
-        int x = 0;
-#pragma unroll
-        for (int bit = 16; bit; bit >>= 1)
-            if (sm.pre[x + bit] <= p0) x += bit;
-        int own[kE];
-        bool lv[kE], first[kE];
-        int2 ev[kE];
-        int32_t nb[kE];
-        {
-            int o = x;
-            uint32_t cend = sm.end[o], cpre = sm.pre[o], cbase = sm.base[o];
-#pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                const uint32_t p = p0 + k;
-                const bool valid = p < total;
-                if (valid)
-                    while (p >= cend) {  // past this list's end (empty lists end where they start)
-                        ++o;
-                        cend = sm.end[o];
-                        cpre = sm.pre[o];
-                        cbase = sm.base[o];
-                    }
-                own[k] = o;
-                first[k] = valid && p == cpre;
-                const uint64_t at = (uint64_t)cbase + (p - cpre);
-                // plain loads: from round 3 on this kernel rewrites the lists behind the reads
-                ev[k] = valid ? src[at] : make_int2(0, 0);
-                if (kPairs) nb[k] = valid ? nsrc[at] : 0;
-                lv[k] = valid;
-            }
-        }
-        if (r > 1) {
-#pragma unroll
-            for (int k = 0; k < kE; ++k)
-                lv[k] = lv[k] && (kPairs ? __ldg(a.vmatch + nb[k]) == 0 : __ldg(a.alive + ev[k].x) != 0);
-        }
-        // the run's pieces: maximum key and live count per list, each piece
-        // folded into its list's shared entries with one atomic
-        uint32_t lcnt = 0;
-        {
-            unsigned long long m = 0;
-            uint32_t c = 0;
-            int co = own[0];
-#pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                if (own[k] != co) {
-                    if (c) {
-                        atomicMax(&sm.best[co], m);
-                        atomicAdd(&sm.live[co], c);
-                    }
-                    co = own[k];
-                    m = 0;
-                    c = 0;
-                }
-                if (lv[k]) {
-                    const unsigned long long key = scan_key(cr, a.noise_scale, (uint32_t)ev[k].x,
-                                                            __int_as_float(ev[k].y));
-                    m = key > m ? key : m;
-                    ++c;
-                }
-                lcnt += lv[k] ? 1u : 0u;
-            }
-            scanned += p0 < total ? min(total - p0, (uint32_t)kE) : 0u;
-            if (c) {
-                atomicMax(&sm.best[co], m);
-                atomicAdd(&sm.live[co], c);
-            }
-        }
-        if (r > 1) {  // compaction
-            const uint32_t incl = warp_inclusive_scan(lcnt);
-            const uint32_t g0 = gbase + incl - lcnt;  // live entries of the tile before this lane's run
-            uint32_t g = g0;
-#pragma unroll
-            for (int k = 0; k < kE; ++k) {
-                if (first[k]) sm.gst[own[k]] = g;
-                g += lv[k] ? 1u : 0u;
-            }
-            __syncwarp();  // every read of this batch and every list start precede the writes
-            g = g0;
-#pragma unroll
-            for (int k = 0; k < kE; ++k)
-                if (lv[k]) {
-                    const uint64_t at = (uint64_t)sm.base[own[k]] + (g - sm.gst[own[k]]);
-                    dst[at] = ev[k];
-                    if (kPairs) ndst[at] = nb[k];
-                    ++g;
-                }
-            gbase += __shfl_sync(kFull, incl, 31);
-        }
-        __syncwarp();
-    }
-    best = sm.best[lane];
-    live = sm.live[lane];
-    __syncwarp();  // the next tile rewrites the shared state
-}
+constexpr int kFlatSpan = 192;            // round 1: a chunk's vertex offsets staged in shared memory up to this many
 
 // Round 1 of the re-randomised rounds: every entry is live, so each
 // vertex's largest key is a plain maximum over its whole list. The lists
@@ -388,7 +203,6 @@ __device__ __forceinline__ void scan_tile(const RoundArgs &a, int r, const int2 
 // vertex's largest key with a 64-bit atomicMax (rbest starts at 0), one per
 // warp when the whole chunk lies inside one list. The proposals follow in
 // k_rpropose; nothing else is written.
-template <bool kPairs>
 __device__ __forceinline__ void flat_round1(const RoundArgs &a, uint32_t *s_off) {
     // list positions are below kappa < 2^32: 32-bit arithmetic throughout
     const int lane = threadIdx.x & 31;
@@ -492,267 +306,63 @@ __device__ __forceinline__ void flat_round1(const RoundArgs &a, uint32_t *s_off)
     }
 }
 
-// a1 of a re-randomised round for the vertices of the active list. The
-// regions are those of the fixed-order loop; warps of a persistent grid
-// take them one at a time from a counter, so that regions with long lists
-// do not leave other warps idle.
-template <bool kPairs>
-__global__ void __launch_bounds__(kT, 4) k_rargmax(RoundArgs a) {
-    __shared__ TileSmem s_tile[kT / 32];
-    DevState *st = a.st;
-    const int r = st->round;
-    const int par = st->parity;
-    const int32_t *in = par ? a.list1 : a.list0;
-    int32_t *out = par ? a.list0 : a.list1;
-    const uint32_t *cnt_in = a.lcnt + (size_t)par * a.nregions;
-    uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
-    // round 1 keeps every entry: it reads the immutable lists and writes
-    // nothing; round 2 compacts them into the working copy; later rounds
-    // compact the working copy in place
-    const int2 *src = r <= 2 ? a.vadjE : a.vadjR;
-    int2 *dst = a.vadjR;
-    const int32_t *nsrc = r <= 2 ? a.vnbrE : a.vnbrR;  // graphs
-    int32_t *ndst = a.vnbrR;
-    if (r == 1) {  // uniform: round 1 is a flat scan of every list (k_rpropose builds the kept list)
-        flat_round1<kPairs>(a, reinterpret_cast<uint32_t *>(&s_tile[threadIdx.x >> 5]));
-        return;
-    }
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = lanemask_lt();
-    unsigned long long scanned = 0, nlive = 0;
-    for (;;) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(&st->rgrab, 1u);
-        g = __shfl_sync(kFull, g, 0);
-        if (g >= a.nregions) break;
-        const uint64_t base = (uint64_t)g * a.region;
-        uint32_t count;
-        if (r == 1) {
-            const int64_t left = a.n - (int64_t)base;
-            count = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.region ? left : (int64_t)a.region);
-        } else {
-            count = cnt_in[g];
-        }
-        uint32_t kept = 0;
-        for (uint32_t i0 = 0; i0 < count; i0 += 32) {
-            const uint32_t i = i0 + lane;
-            const bool ok = i < count;
-            const int32_t v = ok ? (r == 1 ? (int32_t)(base + i) : in[base + i]) : 0;
-            const bool mine = kPairs && ok && __ldg(a.vmatch + v) != 0;  // graphs: v is matched
-            const int4 rec = ok ? a.vrec[v] : make_int4(kCurNone, 0, 0, 0);
-            const bool act = rec.x >= 0 && !mine;
-            const bool lng = act && (uint32_t)rec.w > kLong;
-            if (lng) {  // queue slot and first chunk from one atomic, so both ascend together
-                const uint32_t nch = ((uint32_t)rec.w + kChunk - 1) / kChunk;
-                const unsigned long long old = atomicAdd(&st->lpack, (1ull << 32) | nch);
-                const uint32_t slot = (uint32_t)(old >> 32);
-                if (slot < a.lq_cap) a.lq[slot] = make_int2(v, (int32_t)(uint32_t)old);
-                else st->fault = 3;
-                a.rbest[v] = 0;  // k_rlong folds the chunks' maxima in
-            }
-            // the short and medium lists of the tile as one sequence
-            const uint32_t L = act && !lng ? (uint32_t)rec.w : 0u;
-            unsigned long long best = 0;
-            uint32_t live = 0;
-            scan_tile<kPairs>(a, r, src, dst, nsrc, ndst, L, (uint32_t)rec.z, s_tile[threadIdx.x >> 5], best, live,
-                              scanned);
-            // the vertex's best key goes to k_rpropose, which makes every
-            // proposal of the round (a dependent chain of random reads that
-            // would otherwise sit in this scan's critical path)
-            bool keep = false;
-            if (act && !lng) {
-                if (r > 1) clear_previous(a, r, rec.x);  // T[v] of the previous round is what v counted there
-                a.rbest[v] = best;
-                if (best != 0) {
-                    reinterpret_cast<int2 *>(a.vrec + v)[1] = make_int2(rec.z, (int32_t)live);
-                    keep = true;
-                    nlive += live;
-                } else {
-                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurNone, 0);
-                }
-            }
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (keep) out[base + kept + __popc(km & lt)] = v;
-            kept += __popc(km);
-            const unsigned lgm = __ballot_sync(kFull, lng);  // long lists stay; k_rpropose may drop them
-            if (lng) out[base + kept + __popc(lgm & lt)] = v;
-            kept += __popc(lgm);
-        }
-        if (lane == 0) {
-            cnt_out[g] = kept;
-            if (kept) atomicAdd(&st->cnt[par ^ 1], kept);
-        }
-    }
-    warp_add_u64(scanned, &st->adv);
-    warp_add_u64(nlive, &st->live);
+// Round 1's scan: one flat pass over every list.
+__global__ void __launch_bounds__(kT) k_rflat(RoundArgs a) {
+    __shared__ uint32_t s_off[kT / 32][kFlatSpan];
+    flat_round1(a, s_off[threadIdx.x >> 5]);
 }
 
-// Chunks of the long lists: one warp per chunk of kChunk entries, maximum
-// key of the live entries combined per list with atomicMax.
-template <bool kPairs>
-__global__ void __launch_bounds__(kT) k_rlong(RoundArgs a) {
-    __shared__ unsigned long long s_red[kT / 32];
-    DevState *st = a.st;
-    const unsigned long long lp = st->lpack;
-    const uint32_t nl = (uint32_t)(lp >> 32), nchunks = (uint32_t)lp;
-    unsigned long long scanned = 0, nlive = 0;
-    if (nl > 0 && nl <= a.lq_cap) {
-        const int r = st->round;
-        const int lane = threadIdx.x & 31;
-        const uint32_t warp = (blockIdx.x * kT + threadIdx.x) >> 5;
-        const uint32_t nwarps = (gridDim.x * kT) >> 5;
-        for (uint32_t c = warp; c < nchunks; c += nwarps) {
-            uint32_t lo = 0, hi = nl - 1;  // the last list whose first chunk is <= c
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if ((uint32_t)a.lq[mid].y <= c) lo = mid; else hi = mid - 1;
-            }
-            const int2 q = a.lq[lo];  // {vertex, its first chunk}
-            const int4 rec = a.vrec[q.x];
-            const int64_t lb = (int64_t)(uint32_t)rec.z;
-            const int64_t b = lb + (int64_t)(c - (uint32_t)q.y) * kChunk;
-            const int64_t e = min(lb + (int64_t)(uint32_t)rec.w, b + (int64_t)kChunk);
-            unsigned long long mx = 0;
-            const uint64_t cr = round_counter_base(a.noise_s0, r);
-            int64_t p = b + lane;
-            for (; p + 96 < e; p += 128) {  // four entries per lane in flight
-                int2 x[4];
-                bool lv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = __ldg(a.vadjE + p + 32 * u);  // long lists are never compacted
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    lv[u] = r == 1 || (kPairs ? __ldg(a.vmatch + __ldg(a.vnbrE + p + 32 * u)) == 0
-                                              : __ldg(a.alive + x[u].x) != 0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (lv[u]) {
-                        const unsigned long long k = scan_key(cr, a.noise_scale, (uint32_t)x[u].x,
-                                                              __int_as_float(x[u].y));
-                        if (k > mx) mx = k;
-                        ++nlive;
-                    }
-            }
-            for (; p < e; p += 32) {
-                const int2 x = __ldg(a.vadjE + p);
-                if (r == 1 || (kPairs ? __ldg(a.vmatch + __ldg(a.vnbrE + p)) == 0 : __ldg(a.alive + x.x) != 0)) {
-                    const unsigned long long k = scan_key(cr, a.noise_scale, (uint32_t)x.x, __int_as_float(x.y));
-                    if (k > mx) mx = k;
-                    ++nlive;
-                }
-            }
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(kFull, mx, d);
-                if (y > mx) mx = y;
-            }
-            if (lane == 0) {
-                if (mx) atomicMax(a.rbest + q.x, mx);
-                scanned += (unsigned long long)(e - b);
-            }
-        }
-    }
-    block_add_u64(scanned, s_red, &st->adv);
-    block_add_u64(nlive, s_red, &st->live);
-}
-
-// Every proposal of the round: for each vertex the argmax step kept (one
-// warp per region of the kept list), its largest key of the round (rbest,
-// from the scan or from the chunks of a long list) names its new T[v]; the
-// vertex counts itself in P_r of that edge, and the count that completes the
-// edge makes it a winner. A long list with nothing live left drops out here
-// (T[v] = none; the vertex leaves the active count). Winners are staged per
-// region and appended with one atomic.
+// Round 1's proposals: for every vertex with a list (the flat scan left its
+// largest key in rbest), T[v] is the edge of that key; the vertex counts
+// itself in that edge's P counter, and the count that completes the edge
+// makes it a winner. Winners are staged per region of vertices and
+// appended with one atomic. The vertices that proposed are listed (the
+// kept list, which the statistics of the profiled replay read).
 __global__ void __launch_bounds__(kT) k_rpropose(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
-    const int r = st->round, par = st->parity;
-    int32_t *out = par ? a.list0 : a.list1;
-    uint32_t *cnt_out = a.lcnt + (size_t)(par ^ 1) * a.nregions;
+    int32_t *out = a.list1;
+    uint32_t *cnt_out = a.lcnt + a.nregions;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
     unsigned long long props = 0;
-    if (r == 1) {  // uniform: the flat scan left every vertex's largest key; keep those with a list
-        int32_t *keep_out = out;
-        for (uint64_t g = warp; g < a.nregions; g += nwarps) {
-            const uint64_t base = g * a.region;
-            const int64_t left = a.n - (int64_t)base;
-            const uint32_t c = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.region ? left : (int64_t)a.region);
-            uint32_t won = 0, kept = 0;
-            for (uint32_t i0 = 0; i0 < c; i0 += 32) {
-                const uint32_t i = i0 + lane;
-                bool w = false, keep = false;
-                int32_t nb = -1;
-                const int32_t v = (int32_t)(base + i);
-                if (i < c) {
-                    const unsigned long long best = a.rbest[v];
-                    if (best != 0) {
-                        const int32_t e = edge_of_key(best);  // T[v], input id
-                        reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(e, 0);
-                        w = propose(a, r, e);
-                        if (w) nb = __ldg(a.jof + e);
-                        keep = true;
-                        ++props;
-                    }
-                }
-                const unsigned km = __ballot_sync(kFull, keep);
-                if (keep) keep_out[base + kept + __popc(km & lt)] = v;
-                kept += __popc(km);
-                const unsigned wm = __ballot_sync(kFull, w);
-                if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
-                won += __popc(wm);
-            }
-            if (lane == 0) {
-                cnt_out[g] = kept;
-                if (kept) atomicAdd(&st->cnt[par ^ 1], kept);
-            }
-            if (won) flush_winners(a, base, won);
-        }
-        block_add_u64(props, s_red, &st->proposals);
-        return;
-    }
     for (uint64_t g = warp; g < a.nregions; g += nwarps) {
-        const uint32_t c = cnt_out[g];
         const uint64_t base = g * a.region;
-        uint32_t won = 0;
+        const int64_t left = a.n - (int64_t)base;
+        const uint32_t c = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.region ? left : (int64_t)a.region);
+        uint32_t won = 0, kept = 0;
         for (uint32_t i0 = 0; i0 < c; i0 += 32) {
             const uint32_t i = i0 + lane;
-            bool w = false;
+            bool w = false, keep = false;
             int32_t nb = -1;
+            const int32_t v = (int32_t)(base + i);
             if (i < c) {
-                const int32_t v = out[base + i];
                 const unsigned long long best = a.rbest[v];
-                const int4 rec = a.vrec[v];
-                // a long list (never compacted: its length field stays above
-                // kLong) clears what it counted in the previous round here
-                if ((uint32_t)rec.w > kLong && r > 1) clear_previous(a, r, rec.x);
-                if (best == 0) {  // a long list with nothing live left
-                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(kCurNone, 0);
-                    atomicSub(&st->cnt[par ^ 1], 1u);
-                } else {
+                if (best != 0) {
                     const int32_t e = edge_of_key(best);  // T[v], input id
                     reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(e, 0);
-                    w = propose(a, r, e);
+                    w = propose(a, e);
                     if (w) nb = __ldg(a.jof + e);  // winners are listed by relabelled id
+                    keep = true;
                     ++props;
                 }
             }
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (keep) out[base + kept + __popc(km & lt)] = v;
+            kept += __popc(km);
             const unsigned wm = __ballot_sync(kFull, w);
             if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
             won += __popc(wm);
         }
+        if (lane == 0) {
+            cnt_out[g] = kept;
+            if (kept) atomicAdd(&st->cnt[1], kept);
+        }
         if (won) flush_winners(a, base, won);
     }
     block_add_u64(props, s_red, &st->proposals);
-}
-
-// Graphs: the other endpoint of every list entry (the second word of the
-// fixed order's {edge, endpoint} pairs, in the same list order).
-__global__ void __launch_bounds__(kT) k_pair_endpoints(const int2 *vpair, uint64_t kappa, int32_t *vnbrE) {
-    for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += (uint64_t)gridDim.x * kT)
-        vnbrE[i] = vpair[i].y;
 }
 
 // Round 1's flat scan: the vertex whose list holds entry c * kFlatW, for
@@ -771,26 +381,339 @@ __global__ void __launch_bounds__(kT) k_vchunk(const int64_t *voff, int64_t n, u
 }
 
 // The proposal words' start value by input id: |e| in the upper half.
-__global__ void __launch_bounds__(kT) k_size_words(const int32_t *order, const int64_t *eoffj, int64_t m, int graph,
+__global__ void __launch_bounds__(kT) k_size_words(const int32_t *order, const int64_t *eoffj, int64_t m,
                                                    uint32_t *S32, unsigned long long *S64) {
     for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
         const int32_t e = __ldg(order + j);
-        const uint64_t size = graph ? 2u : (uint64_t)(eoffj[j + 1] - eoffj[j]);
+        const uint64_t size = (uint64_t)(eoffj[j + 1] - eoffj[j]);
         if (S32) S32[e] = (uint32_t)size << 16;
         else S64[e] = (unsigned long long)size << 32;
     }
 }
 
-// Lists as {input edge id, bits(base priority)} pairs, both copies, and
-// the inverse of the edge order (built once per handle).
+// ---------------------------------------------------------------- edge rounds
+
+// Loads the pins of a small edge (size <= kSmall) into registers.
+__device__ __forceinline__ void load_small(const int32_t *__restrict__ pinsj, uint32_t start, uint32_t size,
+                                           int32_t (&pv)[kSmall]) {
+#pragma unroll
+    for (int k = 0; k < kSmall; ++k) pv[k] = (uint32_t)k < size ? __ldg(pinsj + start + k) : 0;
+}
+
+// Step 1 of round r >= 2 (see the file comment). Past the round cap the
+// kernel only counts the live edges (the round end decides between done and
+// HM_ETIMEOUT) and writes nothing. The next record of a region is loaded
+// while the current one is worked on.
+template <bool kPairs>
+__global__ void __launch_bounds__(kT) k_epush(RoundArgs a) {
+    __shared__ unsigned long long s_red[kT / 32];
+    DevState *st = a.st;
+    const int r = st->round;
+    const bool over = r > a.cap;
+    const bool first = r == 2;
+    const bool by_flag = first && !kPairs;
+    const int4 *__restrict__ in = first ? a.erec : a.elist[(r - 1) & 1];
+    const uint32_t *cnt_in = a.ecnt + (size_t)((r - 1) & 1) * a.eregions;
+    int4 *__restrict__ out = a.elist[r & 1];
+    uint32_t *cnt_out = a.ecnt + (size_t)(r & 1) * a.eregions;
+    unsigned long long *cur = (r & 1) ? a.rbest : a.rbest2;
+    const uint64_t cr = round_counter_base(a.noise_s0, r);
+    const float scale = a.noise_scale;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint32_t warp = (blockIdx.x * (uint32_t)kT + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * (uint32_t)kT) >> 5;
+    unsigned long long nedges = 0, npins = 0, nscan = 0, ndead = 0;
+    for (uint32_t g = warp; g < a.eregions; g += nwarps) {  // uniform in the warp
+        const uint64_t base = (uint64_t)g * a.eregion;
+        uint32_t cnt;
+        if (first) {
+            const int64_t left = a.m - (int64_t)base;
+            cnt = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.eregion ? left : (int64_t)a.eregion);
+        } else {
+            cnt = cnt_in[g];
+        }
+        uint32_t kept = 0;
+        int4 nrec = lane < cnt ? in[base + lane] : make_int4(0, 0, 0, 0);
+        for (uint32_t i0 = 0; i0 < cnt; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool ok = i < cnt;
+            const int4 rec = nrec;
+            if (i + 32 < cnt) nrec = in[base + i + 32];
+            const uint32_t start = (uint32_t)rec.z, size = ok ? (uint32_t)rec.w : 0u;
+            const bool big = size > (uint32_t)kSmall;
+            bool live = ok;
+            int32_t pv[kSmall];
+            if (by_flag) {
+                live = ok && a.alive[rec.x] != 0;
+                if (live && !big) load_small(a.pinsj, start, size, pv);
+                if (live) nscan += size;
+            } else {
+                if (ok && !big) {
+                    load_small(a.pinsj, start, size, pv);
+                    bool any = false;
+#pragma unroll
+                    for (int k = 0; k < kSmall; ++k)
+                        if ((uint32_t)k < size) any |= a.vmatch[pv[k]] != 0;
+                    live = !any;
+                }
+                nscan += size;
+                unsigned bm = __ballot_sync(kFull, ok && big);
+                while (bm) {  // the warp tests each big edge's pins together
+                    const int k = __ffs(bm) - 1;
+                    bm &= bm - 1;
+                    const uint32_t bs = __shfl_sync(kFull, start, k), bn = __shfl_sync(kFull, size, k);
+                    bool any = false;
+                    for (uint32_t p = lane; p < bn; p += 32) any |= a.vmatch[__ldg(a.pinsj + bs + p)] != 0;
+                    const bool dead = __any_sync(kFull, any);
+                    if (lane == k) live = !dead;
+                }
+                if (ok && !live) ndead += size;
+            }
+            if (live) {
+                nedges += 1;
+                npins += size;
+            }
+            if (over) continue;  // uniform
+            // this round's live list: compacted to the front of the same region
+            const unsigned lm = __ballot_sync(kFull, live);
+            if (live) out[base + kept + __popc(lm & lt)] = rec;
+            kept += __popc(lm);
+            // every live edge offers its key to each of its pins
+            const unsigned long long key = scan_key(cr, scale, (uint32_t)rec.x, __int_as_float(rec.y));
+            if (live && !big) {
+#pragma unroll
+                for (int k = 0; k < kSmall; ++k)
+                    if ((uint32_t)k < size) atomicMax(cur + pv[k], key);
+            }
+            unsigned bm = __ballot_sync(kFull, live && big);
+            while (bm) {
+                const int k = __ffs(bm) - 1;
+                bm &= bm - 1;
+                const uint32_t bs = __shfl_sync(kFull, start, k), bn = __shfl_sync(kFull, size, k);
+                const unsigned long long kk = __shfl_sync(kFull, key, k);
+                for (uint32_t p = lane; p < bn; p += 32) atomicMax(cur + __ldg(a.pinsj + bs + p), kk);
+            }
+        }
+        if (lane == 0 && !over) cnt_out[g] = kept;
+    }
+    block_add_u64(nedges, s_red, &st->ledges);
+    block_add_u64(npins, s_red, &st->lpins);
+    block_add_u64(nscan, s_red, &st->adv);
+    block_add_u64(ndead, s_red, &st->kills);
+}
+
+// The end of an edge round (one thread, after every block of k_ewin has
+// finished): records the round and decides whether another one runs. A
+// round with no live edge did not happen (the one before ended the
+// matching); past the cap, a live edge means HM_ETIMEOUT.
+__device__ void eround_end(const RoundArgs &a) {
+    DevState *st = a.st;
+    const int r = st->round;
+    const uint32_t nw = st->nwin;
+    const unsigned long long ledges = st->ledges;
+    int cont = 0;
+    if (r > a.cap) {
+        st->rounds_done = r - 1;
+        if (ledges > 0) st->status = HM_ETIMEOUT;
+    } else {
+        // proposals: the keys offered (one per live pin). The vertices
+        // offered a key (active, next) and their degrees are counted by the
+        // profiled replay (k_ekept), which also records the live edges and
+        // pins, as in round 1
+        const bool prof = a.profiled != 0;
+        write_stats_row(a, r, 0, nw, 0u, st->adv, st->lpins, st->winpins, st->kills, 0u, st->lpins, 0ull,
+                        prof ? ledges : 0ull, prof ? st->lpins : 0ull);
+        if (st->fault) {
+            st->status = HM_ECUDA;
+        } else if (ledges == 0) {
+            st->rounds_done = r - 1;
+        } else if (nw == 0) {  // the live edge with the largest key always wins: inconsistent input
+            st->rounds_done = r;
+            st->status = HM_EINVAL;
+        } else {
+            st->rounds_done = r;
+            cont = ledges > nw;  // the edges that did not win may still be live
+        }
+    }
+    st->nwin = 0;
+    st->kdone = 0;
+    st->adv = st->kills = st->winpins = st->proposals = 0;
+    st->live = st->kpack = st->sdeg = 0;
+    st->ledges = st->lpins = 0;
+    if (cont) st->round = r + 1;
+    else st->finished = 1;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
+}
+
+// Step 2 of round r >= 2: an edge wins when every pin's slot holds its key;
+// it joins the matching and marks its pins matched. The other buffer is
+// cleared on the way. The block that finishes last (a ticket counter) ends
+// the round.
+template <bool kPairs>
+__global__ void __launch_bounds__(kT) k_ewin(RoundArgs a) {
+    __shared__ unsigned long long s_red[kT / 32];
+    __shared__ int s_last;
+    DevState *st = a.st;
+    const int r = st->round;
+    unsigned long long nw = 0, wp = 0;
+    if (r <= a.cap) {  // uniform
+        const int4 *__restrict__ in = a.elist[r & 1];
+        const uint32_t *cnt_in = a.ecnt + (size_t)(r & 1) * a.eregions;
+        const unsigned long long *cur = (r & 1) ? a.rbest : a.rbest2;
+        unsigned long long *other = (r & 1) ? a.rbest2 : a.rbest;
+        // the other buffer must be zero at every vertex the next round
+        // offers a key to, and nonzero only there afterwards (the vertex
+        // state reads it): cleared whole, one streaming pass of 8n bytes
+        // (a round with no live edge ends the matching and keeps it)
+        if (st->lpins > 0) {
+            ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(other);  // cudaMalloc'd: 16-byte aligned
+            const uint64_t n2 = (uint64_t)a.n / 2;
+            for (uint64_t x = blockIdx.x * (uint64_t)kT + threadIdx.x; x < n2; x += (uint64_t)gridDim.x * kT)
+                o2[x] = make_ulonglong2(0ull, 0ull);
+            if (blockIdx.x == 0 && threadIdx.x == 0 && (a.n & 1)) other[a.n - 1] = 0;
+        }
+        const uint64_t cr = round_counter_base(a.noise_s0, r);
+        const float scale = a.noise_scale;
+        const int lane = threadIdx.x & 31;
+        const uint32_t warp = (blockIdx.x * (uint32_t)kT + threadIdx.x) >> 5;
+        const uint32_t nwarps = (gridDim.x * (uint32_t)kT) >> 5;
+        for (uint32_t g = warp; g < a.eregions; g += nwarps) {  // uniform in the warp
+            const uint32_t cnt = cnt_in[g];
+            for (uint32_t i0 = 0; i0 < cnt; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                const bool ok = i < cnt;
+                const int4 rec = ok ? in[(uint64_t)g * a.eregion + i] : make_int4(0, 0, 0, 0);
+                const uint32_t start = (uint32_t)rec.z, size = ok ? (uint32_t)rec.w : 0u;
+                const bool big = size > (uint32_t)kSmall;
+                const unsigned long long key = scan_key(cr, scale, (uint32_t)rec.x, __int_as_float(rec.y));
+                bool win = ok;
+                int32_t pv[kSmall];
+                if (ok && !big) {
+                    load_small(a.pinsj, start, size, pv);
+#pragma unroll
+                    for (int k = 0; k < kSmall; ++k)
+                        if ((uint32_t)k < size) {
+                            win &= cur[pv[k]] == key;
+                        }
+                }
+                unsigned bm = __ballot_sync(kFull, ok && big);
+                while (bm) {  // the warp tests each big edge's pins together
+                    const int k = __ffs(bm) - 1;
+                    bm &= bm - 1;
+                    const uint32_t bs = __shfl_sync(kFull, start, k), bn = __shfl_sync(kFull, size, k);
+                    const unsigned long long kk = __shfl_sync(kFull, key, k);
+                    bool miss = false;
+                    for (uint32_t p = lane; p < bn; p += 32) {
+                        const int32_t v = __ldg(a.pinsj + bs + p);
+                        miss |= cur[v] != kk;
+                    }
+                    const bool lost = __any_sync(kFull, miss);
+                    if (lane == k) win = !lost;
+                }
+                if (win) {
+                    a.inM[rec.x] = 1;
+                    if (a.wround) a.wround[rec.x] = r;
+                    nw += 1;
+                    wp += size;
+                    if (!big) {
+#pragma unroll
+                        for (int k = 0; k < kSmall; ++k)
+                            if ((uint32_t)k < size) a.vmatch[pv[k]] = 1;
+                    }
+                }
+                bm = __ballot_sync(kFull, win && big);
+                while (bm) {  // a big winner's pins, marked by the warp
+                    const int k = __ffs(bm) - 1;
+                    bm &= bm - 1;
+                    const uint32_t bs = __shfl_sync(kFull, start, k), bn = __shfl_sync(kFull, size, k);
+                    for (uint32_t p = lane; p < bn; p += 32) a.vmatch[__ldg(a.pinsj + bs + p)] = 1;
+                }
+            }
+        }
+    }
+    {
+        uint32_t x = (uint32_t)nw;  // winners: one atomic per warp
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&st->nwin, x);
+    }
+    block_add_u64(wp, s_red, &st->winpins);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->kdone, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        eround_end(a);
+    }
+}
+
+// Profiled edge rounds only, after round r's k_ewin: the vertices offered a
+// key in round r (the pins of its live edges: the vertices active at its
+// start, unmatched with a live edge), counted as both the active and the
+// kept vertices, and the sum of their degrees, added to round r's stats row
+// (zero there until now).
+__global__ void __launch_bounds__(kT) k_ekept(RoundArgs a, int r) {
+    __shared__ unsigned long long s_red[kT / 32];
+    const unsigned long long *cur = (r & 1) ? a.rbest : a.rbest2;
+    unsigned long long kept = 0, deg = 0;
+    for (int64_t v = blockIdx.x * (int64_t)kT + threadIdx.x; v < a.n; v += (int64_t)gridDim.x * kT) {
+        if (cur[v] == 0) continue;
+        kept += 1;
+        deg += (unsigned long long)(a.voff[v + 1] - a.voff[v]);
+    }
+    if (r - 1 < kStatRounds) {
+        int64_t *row = a.stats + (int64_t)(r - 1) * HM_STATS_COLS;
+        block_add_u64(kept, s_red, reinterpret_cast<unsigned long long *>(row + HM_STAT_ACTIVE));
+        block_add_u64(kept, s_red, reinterpret_cast<unsigned long long *>(row + HM_STAT_NEXT));
+        block_add_u64(deg, s_red, reinterpret_cast<unsigned long long *>(row + HM_STAT_DEG));
+    }
+}
+
+// The per-vertex state after the last round run: HM_VERTEX_MATCHED, T[v]
+// (input id) or HM_VERTEX_NONE. After round 1 it is the round-1 record;
+// after an edge round R, T[v] is the edge of v's slot in round R's buffer
+// (zero: v was offered no key in round R).
+__global__ void __launch_bounds__(kT) k_rvertex_state(RoundArgs a, int32_t *out) {
+    const int R = a.st->rounds_done;
+    const unsigned long long *buf = (R & 1) ? a.rbest : a.rbest2;
+    for (int64_t v = blockIdx.x * (int64_t)kT + threadIdx.x; v < a.n; v += (int64_t)gridDim.x * kT) {
+        const int32_t t = a.vrec[v].x;
+        int32_t s;
+        if (a.vmatch[v] || t == kCurMatched) {
+            s = HM_VERTEX_MATCHED;
+        } else if (R <= 1) {
+            s = t >= 0 ? t : HM_VERTEX_NONE;
+        } else {
+            const unsigned long long k = buf[v];
+            s = k != 0 ? edge_of_key(k) : HM_VERTEX_NONE;
+        }
+        out[v] = s;
+    }
+}
+
+// Every edge as {input id, bits(base priority), first pin, size}, in j order
+// (the input of round 2).
+__global__ void __launch_bounds__(kT) k_erec(const int32_t *order, const int64_t *eoffj, const float *w, int64_t m,
+                                           int graph, int4 *erec) {
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
+        const int32_t e = __ldg(order + j);
+        const int64_t b = graph ? 2 * j : eoffj[j];
+        const int64_t s = graph ? 2 : eoffj[j + 1] - b;
+        erec[j] = make_int4(e, __float_as_int(w ? __ldg(w + e) : 1.0f), (int32_t)(uint32_t)b, (int32_t)s);
+    }
+}
+
+// Lists as {input edge id, bits(base priority)} pairs, and the inverse of
+// the edge order (built once per handle).
 __global__ void __launch_bounds__(kT) k_map(const int32_t *order, const int32_t *vadj, const float *w, int64_t m,
-                                          uint64_t kappa, int2 *vadjE, int2 *vadjR, int32_t *jof) {
+                                          uint64_t kappa, int2 *vadjE, int32_t *jof) {
     const uint64_t stride = (uint64_t)gridDim.x * kT;
     for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += stride) {
         const int32_t e = __ldg(order + __ldg(vadj + i));
-        const int2 x = make_int2(e, __float_as_int(w ? __ldg(w + e) : 1.0f));
-        vadjE[i] = x;
-        vadjR[i] = x;
+        vadjE[i] = make_int2(e, __float_as_int(w ? __ldg(w + e) : 1.0f));
     }
     for (uint64_t j = blockIdx.x * (uint64_t)kT + threadIdx.x; j < (uint64_t)m; j += stride)
         jof[order[j]] = (int32_t)j;
@@ -809,12 +732,10 @@ int fit_per_sm(K kernel) {
 RoundArgs rand_args(const Handle *h) {
     RoundArgs a = round_args(h);
     a.vrec = h->vrecR;
-    a.pairs = h->graph ? 1 : 0;  // graphs: liveness from vmatch, flag-only win, no kill
-    a.vnbrE = h->vnbrE;
-    a.vnbrR = h->vnbrR;
-    a.vadj = reinterpret_cast<const int32_t *>(h->vadjR);  // for the kill step: stride 2
+    a.pairs = h->graph ? 1 : 0;  // graphs: round 1 sets matched flags and needs no kill
+    a.vmatch = h->graph ? h->vmatch : h->rmatch;
+    a.vadj = reinterpret_cast<const int32_t *>(h->vadjE);  // round 1's kill step: every second word
     a.vadjE = h->vadjE;
-    a.vadjR = h->vadjR;
     a.noise_scale = h->noise * (1.0f / 16777216.0f);
     a.noise_s0 = splitmix64_first(h->seed);
     a.jof = h->jof;
@@ -823,13 +744,19 @@ RoundArgs rand_args(const Handle *h) {
     a.w64 = h->p16 ? 0 : 1;
     a.S32 = h->S32;
     a.S64 = h->S64;
-    a.W64a = h->W64a;
-    a.W64b = h->W64b;
+    a.W64 = h->W64;
     a.vchunk = h->vchunk;
     a.kappa = h->kappa;
-    a.lq = h->lq;
     a.rbest = h->rbest;
-    a.lq_cap = h->lq_cap;
+    a.rbest2 = h->rbest2;
+    a.erec = h->erec;
+    a.elist[0] = h->elist0;
+    a.elist[1] = h->elist1;
+    a.ecnt = h->ecnt;
+    a.eregions = h->eregions;
+    a.eregion = h->eregion;
+    a.erounds = 1;
+    a.profiled = 0;
     return a;
 }
 
@@ -837,30 +764,42 @@ unsigned rinit_grid(const Handle *h) {
     return grid_for((uint64_t)std::max(h->n, h->m), kT, h->sm_count, 16);
 }
 
-void launch_rinit(const Handle *h, const RoundArgs &a, cudaStream_t s) {
-    k_rinit<<<rinit_grid(h), kT, 0, s>>>(a);
-}
-
-void launch_rround(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
+// Round 1 (vertex-driven; the kill kernel's last block ends it). ev (or
+// null): the profiled replay's events, as in the fixed order's rounds.
+void launch_round1(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], s);
-    if (a.pairs) {
-        k_rargmax<true><<<h->rargmax_grid, kT, 0, s>>>(a);
-        k_rlong<true><<<h->rlong_grid, kT, 0, s>>>(a);
-    } else {
-        k_rargmax<false><<<h->rargmax_grid, kT, 0, s>>>(a);
-        k_rlong<false><<<h->rlong_grid, kT, 0, s>>>(a);
-    }
+    k_rflat<<<h->rflat_grid, kT, 0, s>>>(a);
     k_rpropose<<<h->rpropose_grid, kT, 0, s>>>(a);
     if (ev) launch_kept_degrees(h, a, s, ev, 1);
     launch_win_kill_end(h, a, s, ev, 2);
 }
 
-void capture_rinit(Handle *h, cudaStream_t s, void *ctx) {
-    launch_rinit(h, *static_cast<const RoundArgs *>(ctx), s);
+// An edge round (round 2 on): the offers, then the win test and the round end.
+void launch_eround(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
+    if (ev) cudaEventRecord(ev[0], s);
+    if (a.pairs) k_epush<true><<<h->epush_grid, kT, 0, s>>>(a);
+    else k_epush<false><<<h->epush_grid, kT, 0, s>>>(a);
+    if (ev) {
+        cudaEventRecord(ev[5], s);
+        cudaEventRecord(ev[1], s);
+    }
+    if (a.pairs) k_ewin<true><<<h->ewin_grid, kT, 0, s>>>(a);
+    else k_ewin<false><<<h->ewin_grid, kT, 0, s>>>(a);
+    if (ev) {  // no kill kernel (the next round's filter finds the deaths); the round end is part of k_ewin
+        cudaEventRecord(ev[2], s);
+        cudaEventRecord(ev[3], s);
+        cudaEventRecord(ev[4], s);
+    }
 }
 
-void capture_rround(Handle *h, cudaStream_t s, void *ctx) {
-    launch_rround(h, *static_cast<const RoundArgs *>(ctx), s, nullptr);
+void capture_rfirst(Handle *h, cudaStream_t s, void *ctx) {
+    const RoundArgs &a = *static_cast<const RoundArgs *>(ctx);
+    k_rinit<<<rinit_grid(h), kT, 0, s>>>(a);
+    launch_round1(h, a, s, nullptr);
+}
+
+void capture_eround(Handle *h, cudaStream_t s, void *ctx) {
+    launch_eround(h, *static_cast<const RoundArgs *>(ctx), s, nullptr);
 }
 
 hm_status build_graph_rand(Handle *h) {
@@ -882,9 +821,9 @@ hm_status build_graph_rand(Handle *h) {
     a.cond = cond;
     a.use_cond = 1;
     cudaGraphNode_t tail = nullptr;
-    hm_status st = capture_chain(h, g, capture_rinit, &a, &tail);
+    hm_status st = capture_chain(h, g, capture_rfirst, &a, &tail);
     if (st != HM_OK) return st;
-    if ((st = add_while_loop(h, g, tail, cond, capture_rround, &a)) != HM_OK) return st;
+    if ((st = add_while_loop(h, g, tail, cond, capture_eround, &a)) != HM_OK) return st;
     if ((e = cudaGraphInstantiate(&h->exec_rand, g, 0)) != cudaSuccess)
         return cuda_fail(e, "cudaGraphInstantiate");
     h->graph_cap_rand = h->cap;
@@ -896,38 +835,44 @@ hm_status build_graph_rand(Handle *h) {
 }  // namespace
 
 hm_status rand_prepare(Handle *h, cudaStream_t s) {
-    h->rargmax_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_rargmax<true>) : fit_per_sm(k_rargmax<false>)));
-    h->rlong_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_rlong<true>) : fit_per_sm(k_rlong<false>)));
+    h->rflat_grid = (unsigned)(h->sm_count * fit_per_sm(k_rflat));
     h->rpropose_grid = (unsigned)(h->sm_count * fit_per_sm(k_rpropose));
+    h->epush_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_epush<true>) : fit_per_sm(k_epush<false>)));
+    h->ewin_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_ewin<true>) : fit_per_sm(k_ewin<false>)));
     if (h->vrecR) return HM_OK;
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
-    h->lq_cap = (uint32_t)(std::min<uint64_t>(n, h->kappa / kLong) + 1);
+    // regions of the edge lists: four per warp of the offer kernel's grid,
+    // whole 32-record steps
+    h->eregions = h->epush_grid * (kT / 32) * 4;
+    h->eregion = (uint32_t)std::max<uint64_t>(32, (m + h->eregions - 1) / h->eregions);
+    h->eregion = (h->eregion + 31) / 32 * 32;
     hm_status st;
     if ((st = dalloc(&h->vrecR, n, s, "re-randomised vertex records")) != HM_OK ||
         (st = dalloc(&h->vadjE, h->kappa, s, "vertex lists in edge ids")) != HM_OK ||
-        (st = dalloc(&h->vadjR, h->kappa, s, "re-randomised vertex lists")) != HM_OK ||
         (st = dalloc(&h->jof, m, s, "inverse edge order")) != HM_OK ||
-        (st = dalloc(&h->P2, m, s, "second proposal counters")) != HM_OK ||
+        (st = dalloc(&h->P2, m, s, "proposal counters")) != HM_OK ||
         (h->p16 && !h->graph && (st = dalloc(&h->S32, m, s, "edge sizes")) != HM_OK) ||
         (!h->p16 && ((st = dalloc(&h->S64, m, s, "edge sizes")) != HM_OK ||
-                     (st = dalloc(&h->W64a, m, s, "proposal counters")) != HM_OK ||
-                     (st = dalloc(&h->W64b, m, s, "proposal counters")) != HM_OK)) ||
-        (st = dalloc(&h->lq, h->lq_cap, s, "long-list queue")) != HM_OK ||
-        (st = dalloc(&h->rbest, n, s, "largest keys of the round")) != HM_OK ||
+                     (st = dalloc(&h->W64, m, s, "proposal counters")) != HM_OK)) ||
+        (st = dalloc(&h->rbest, n, s, "largest keys (odd rounds)")) != HM_OK ||
+        (st = dalloc(&h->rbest2, n, s, "largest keys (even rounds)")) != HM_OK ||
         (st = dalloc(&h->vchunk, (h->kappa + kFlatW - 1) / kFlatW + 1, s, "flat chunk vertices")) != HM_OK ||
-        (h->graph && ((st = dalloc(&h->vnbrE, h->kappa, s, "list endpoints")) != HM_OK ||
-                      (st = dalloc(&h->vnbrR, h->kappa, s, "re-randomised list endpoints")) != HM_OK))) {
+        (st = dalloc(&h->erec, m, s, "edge records")) != HM_OK ||
+        (st = dalloc(&h->elist0, m, s, "live edge list")) != HM_OK ||
+        (st = dalloc(&h->elist1, m, s, "live edge list")) != HM_OK ||
+        (st = dalloc(&h->ecnt, 2 * (uint64_t)h->eregions, s, "live edge list regions")) != HM_OK ||
+        (!h->graph && (st = dalloc(&h->rmatch, n, s, "matched flags")) != HM_OK)) {
         free_rand_buffers(h);
         return st;
     }
-    if (h->graph && h->kappa)  // the endpoints in list order, from the fixed order's pair lists
-        k_pair_endpoints<<<grid_for(h->kappa, kT, h->sm_count, 16), kT, 0, s>>>(h->vpair, h->kappa, h->vnbrE);
     if (m) {
+        const float *w = h->weighted ? h->weights : nullptr;
         k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
-            h->order, h->vadj, h->weighted ? h->weights : nullptr, h->m, h->kappa, h->vadjE, h->vadjR, h->jof);
+            h->order, h->vadj, w, h->m, h->kappa, h->vadjE, h->jof);
+        k_erec<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, w, h->m, h->graph ? 1 : 0,
+                                                               h->erec);
         if (!h->graph)  // graphs count in bytes and need no sizes
-            k_size_words<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->m, 0, h->S32,
-                                                                        h->S64);
+            k_size_words<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->m, h->S32, h->S64);
         const uint64_t nchunks = (h->kappa + kFlatW - 1) / kFlatW;
         if (nchunks)
             k_vchunk<<<grid_for(nchunks, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, h->n, nchunks, h->vchunk);
@@ -952,6 +897,12 @@ hm_status launch_match_graph_rand(Handle *h, cudaStream_t s) {
     return HM_OK;
 }
 
+cudaError_t launch_rand_vertex_state(const Handle *h, int32_t *out_dev, cudaStream_t s) {
+    const RoundArgs a = rand_args(h);
+    k_rvertex_state<<<grid_for((uint64_t)h->n, kT, h->sm_count, 16), kT, 0, s>>>(a, out_dev);
+    return cudaGetLastError();
+}
+
 hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *launches, double *round_ms,
                              int32_t max_rounds) {
     hm_status st = rand_prepare(h, s);
@@ -972,24 +923,33 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
     RoundArgs a = rand_args(h);
     float t = 0;
     cudaEventRecord(ev[5], s);
-    launch_rinit(h, a, s);
+    k_rinit<<<rinit_grid(h), kT, 0, s>>>(a);
     cudaEventRecord(ev[0], s);
     cudaError_t e = cudaEventSynchronize(ev[0]);
     if (e != cudaSuccess) return cuda_fail(e, "profile init");
     cudaEventElapsedTime(&t, ev[5], ev[0]);
     ms[HM_K_INIT] += t;
     launches[HM_K_INIT] += 1;
+    a.profiled = 1;  // the edge rounds record their live edges and pins
     for (int32_t r = 0;; ++r) {
-        launch_live_edges(h, a, s, 1);  // untimed: before the round's first event
-        launch_rround(h, a, s, ev);
+        // per kernel class: launches of round 1 (scan, proposals | win | kill with the round
+        // end | -) and of an edge round (offers | win test with the round end | - | -)
+        static const int kLaunches[2][4] = {{2, 1, 1, 0}, {1, 1, 0, 0}};
+        const int edge = r > 0;
+        if (!edge) {
+            launch_live_edges(h, a, s, 1);  // untimed: before the round's first event
+            launch_round1(h, a, s, ev);
+        } else {
+            launch_eround(h, a, s, ev);
+            k_ekept<<<grid_for((uint64_t)h->n, kT, h->sm_count, 8), kT, 0, s>>>(a, r + 1);  // untimed
+        }
         cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "profile round");
         for (int k = 0; k < 4; ++k) {
             cudaEventElapsedTime(&t, ev[k], k == 0 ? ev[5] : ev[k + 1]);
             ms[HM_K_ARGMAX + k] += t;
-            // the argmax step is three kernels here; the round end is part of the kill kernel
-            launches[HM_K_ARGMAX + k] += k == 0 ? 3 : (k == 3 ? 0 : 1);
+            launches[HM_K_ARGMAX + k] += kLaunches[edge][k];
             if (r < max_rounds) round_ms[(int64_t)r * 4 + k] = t;
         }
         if (h->h_st->finished) break;
@@ -999,24 +959,25 @@ hm_status profile_match_rand(Handle *h, cudaStream_t s, double *ms, int64_t *lau
 }
 
 void free_rand_buffers(Handle *h) {
-    void *bufs[] = {h->vrecR, h->vadjE, h->vadjR, h->jof, h->P2, h->lq, h->rbest, h->vnbrE, h->vnbrR,
-                    h->S32, h->S64, h->W64a, h->W64b, h->vchunk};
+    void *bufs[] = {h->vrecR, h->vadjE, h->jof, h->P2, h->rbest, h->rbest2, h->S32, h->S64, h->W64,
+                    h->vchunk, h->erec, h->elist0, h->elist1, h->ecnt, h->rmatch};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, h->cap_stream);
     h->vrecR = nullptr;
     h->vadjE = nullptr;
-    h->vadjR = nullptr;
     h->jof = nullptr;
     h->P2 = nullptr;
-    h->lq = nullptr;
     h->rbest = nullptr;
+    h->rbest2 = nullptr;
     h->S32 = nullptr;
     h->S64 = nullptr;
-    h->W64a = nullptr;
-    h->W64b = nullptr;
+    h->W64 = nullptr;
     h->vchunk = nullptr;
-    h->vnbrE = nullptr;
-    h->vnbrR = nullptr;
+    h->erec = nullptr;
+    h->elist0 = nullptr;
+    h->elist1 = nullptr;
+    h->ecnt = nullptr;
+    h->rmatch = nullptr;
     if (h->exec_rand) cudaGraphExecDestroy(h->exec_rand);
     h->exec_rand = nullptr;
 }

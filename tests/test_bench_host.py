@@ -65,7 +65,7 @@ def test_traffic_rows_keyed_by_source_workload_and_mode(tmp_path, monkeypatch):
         ("k_argmax", "fixed", "large", h1, 1000, 1, None), ("k_argmax", "fixed", "graph", h1, 2000, 1, None),
         ("k_argmax", "fixed", "large", h1, 111, 4, 50.0),
         ("k_kill", "re-randomised", "large", h1, 3000, 1, None),
-        ("k_rargmax+k_rlong+k_rpropose", "re-randomised", "large", h1r, 4000, 1, None),
+        ("k_rflat+k_rpropose+k_epush", "re-randomised", "large", h1r, 4000, 1, None),
         ("k_win", "fixed", "large", "0000000000000000", 5000, 1, None),
         ("k_kill", "fixed", "large", h1, 600, 4, 200.0)])
     assert bench.measured_traffic("argmax", False) == 1000.0

@@ -433,12 +433,14 @@ def test_graph_cursors_pass_each_entry_once():
 
 
 def test_active_vertices_and_their_degrees_per_round():
-    """The argmax step's count of the vertices it keeps (HM_STAT_NEXT) and the
+    """The count of the vertices kept for each round (HM_STAT_NEXT) and the
     replay's count of their degrees (HM_STAT_DEG) equal, round by round, the
     active vertex sets of the oracle's run and their degree sums, in the
     fixed order and in re-randomised rounds; the replay's live edges and
     live pins at the start of every round (HM_STAT_LEDGES, HM_STAT_LPINS)
-    equal the oracle's. A plain match leaves these three columns at 0."""
+    equal the oracle's. A plain match leaves these three columns at 0, and in
+    re-randomised rounds it counts the kept vertices of round 1 only (later
+    rounds are edge-driven and leave the vertex counts to the replay)."""
     nxt = hmlib.STAT_COLUMNS.index("next")
     dg = hmlib.STAT_COLUMNS.index("deg")
     le = hmlib.STAT_COLUMNS.index("ledges")
@@ -459,7 +461,10 @@ def test_active_vertices_and_their_degrees_per_round():
             mt.profile()
             stats = mt.round_stats()
         assert res.status == OK and res.rounds == o.rounds
-        assert plain[:o.rounds, nxt].tolist() == u and not plain[:, dg].any()
+        if noise:
+            assert plain[0, nxt] == u[0] and not plain[1:, nxt].any() and not plain[:, dg].any()
+        else:
+            assert plain[:o.rounds, nxt].tolist() == u and not plain[:, dg].any()
         assert not plain[:, le].any() and not plain[:, lp].any()
         assert stats[:o.rounds, nxt].tolist() == u
         assert stats[:o.rounds, dg].tolist() == sdeg
