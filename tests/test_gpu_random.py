@@ -116,10 +116,14 @@ def test_degenerate_inputs():
             assert_parity(h, noise)
 
 
-@pytest.mark.parametrize("cap", [1, 2])
+@pytest.mark.parametrize("cap", [1, 2, 3, 5])
 def test_vertex_state_after_capped_rounds(cap):
-    """a1 parity: T[v] after round r is the oracle's argmax of round r."""
-    for h in (synth.small(seed=5, n=5000, m=15_000), hub_graph(6, 20_000, 2, [3000, 5000], 20_000)):
+    """a1 parity: T[v] after round r is the oracle's argmax of round r. Cap 1
+    stops after the vertex-driven round; caps 2, 3 and 5 after an edge round,
+    where the next round only counts the live edges (HM_ETIMEOUT if one is
+    left) and the vertex state is read from that round's key slots."""
+    for h in (synth.small(seed=5, n=5000, m=15_000), hub_graph(6, 20_000, 2, [3000, 5000], 20_000),
+              synth.large(seed=8, n=30_000, m=60_000, kmax=256), synth.rgg(seed=6, n=20_000)):
         res, stats, vs = run_gpu(h, 10.0, cap=cap)
         o = oracle.match(h, max_rounds=cap, noise=10.0)
         assert res.rounds == min(cap, o.rounds)
@@ -147,6 +151,19 @@ def test_switch_modes_and_repeat():
         stats = mt.round_stats()
         assert stats[:rand.rounds, WIN].tolist() == rand.round_stats[:, 2].tolist()
         assert np.all(stats[:rand.rounds, PROPOSALS] > 0)
+
+
+def test_every_live_edge_wins_in_one_round():
+    """Pairwise disjoint edges: all of them win in round 1 and nothing is
+    left (no edge round runs); then a chain whose last edge round ends with
+    every live edge winning."""
+    h = synth.from_edges(12, [[0, 1, 2], [3, 4], [5, 6, 7, 8], [9, 10, 11]], [0.5, 0.25, 0.75, 1.0])
+    for noise in (0.5, 1e3):
+        o = assert_parity(h, noise)
+        assert o.rounds == 1
+    chain = synth.from_edges(40, [[i, i + 1] for i in range(39)], [(i % 7 + 1) / 8 for i in range(39)])
+    for noise in (0.3, 10.0):
+        assert_parity(chain, noise)
 
 
 def test_different_seeds_differ():
