@@ -184,9 +184,8 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
     ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT, LIVE = range(9)
     LEDGES = 10
     pc = 2 if p16 else 4  # bytes of one P counter
-    if random:  # flag, counter word read + write, mask; matched flag, two key slots,
-                # offset pair, first entry, record write
-        init = float(m * (1 + 4 + 4 + 1) + n * (1 + 8 + 8 + 16 + 4 + 16))
+    if random:  # flag, counter word read + write, mask; matched flag, two key slots
+        init = float(m * (1 + 4 + 4 + 1) + n * (1 + 8 + 8))
     elif pairs:  # mask, P copied from its initial copy; matched flags
         init = float(m * (1 + 2 * pc) + n)
     else:       # flag, mask, P copied from its initial copy (read + write)

@@ -148,8 +148,6 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
             a.vmatch[i] = 0;
             a.rbest[i] = 0;   // round 1 folds list pieces into it with atomicMax
             a.rbest2[i] = 0;  // round 2 offers its keys into it
-            const int64_t b = a.voff[i], e = a.voff[i + 1];
-            a.vrec[i] = make_int4(a.firstj[i], 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -707,6 +705,17 @@ __global__ void __launch_bounds__(kT) k_rvertex_state(RoundArgs a, int32_t *out)
     }
 }
 
+// The round-1 vertex records {T[v], 0, list start, list length}, built once
+// per handle: a match rewrites T[v] of every vertex with a list in round 1
+// (k_rpropose) and of the winners' pins (k_win) and nothing else, and a
+// vertex without a list keeps T = none.
+__global__ void __launch_bounds__(kT) k_rrec(const int64_t *voff, int64_t n, int4 *vrec) {
+    for (int64_t v = blockIdx.x * (int64_t)kT + threadIdx.x; v < n; v += (int64_t)gridDim.x * kT) {
+        const int64_t b = voff[v], e = voff[v + 1];
+        vrec[v] = make_int4(kCurNone, 0, (int32_t)(uint32_t)b, (int32_t)(uint32_t)(e - b));
+    }
+}
+
 // Every edge as {input id, bits(base priority), first pin, size}, in j order
 // (the input of round 2).
 __global__ void __launch_bounds__(kT) k_erec(const int32_t *order, const int64_t *eoffj, const float *w, int64_t m,
@@ -878,6 +887,8 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
         free_rand_buffers(h);
         return st;
     }
+    if (n)
+        k_rrec<<<grid_for(n, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, h->n, h->vrecR);
     if (m) {
         const float *w = h->weighted ? h->weights : nullptr;
         k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
