@@ -354,7 +354,7 @@ void free_handle_buffers(Handle *h);
 // a.vadj[p * kill_stride]. ev (or null): events 1-4 of a profiled round.
 // Profiled rounds only: records ev[5] (the end of the argmax span), then
 // counts the degrees of the vertices the argmax step kept (HM_STAT_DEG).
-void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int random);
+void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev);
 // Profiled rounds only, before the round's timed kernels: counts the edges
 // live at the start of the round and their pins (HM_STAT_LEDGES/LPINS).
 void launch_live_edges(const Handle *h, const RoundArgs &a, cudaStream_t s, int random);

@@ -504,11 +504,8 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
 // argmax and win kernels: the sum of the degrees of the vertices the argmax
 // step kept (the unmatched vertices with a live edge), added to the round's
 // counter. The timed match does not run it. The degree comes from the
-// record in the fixed order (a graph's record holds the list end) and from
-// the vertex offsets in the re-randomised rounds (whose records hold the
-// live list length; a long list stays in the kept list with T = kCurNone
-// when nothing of it was live, and is skipped).
-__global__ void __launch_bounds__(kT) k_kept_degrees(RoundArgs a, int random) {
+// vertex record (a graph's record holds the list end).
+__global__ void __launch_bounds__(kT) k_kept_degrees(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
     DevState *st = a.st;
     const int par = st->parity;
@@ -524,8 +521,7 @@ __global__ void __launch_bounds__(kT) k_kept_degrees(RoundArgs a, int random) {
             const int32_t v = out[g * a.region + i];
             const int4 rec = a.vrec[v];
             if (rec.x < 0) continue;
-            if (random) sum += (uint64_t)(a.voff[v + 1] - a.voff[v]);
-            else sum += a.pairs ? (uint32_t)rec.z - (uint64_t)a.voff[v] : (uint32_t)rec.w;
+            sum += a.pairs ? (uint32_t)rec.z - (uint64_t)a.voff[v] : (uint32_t)rec.w;
         }
     }
     block_add_u64(sum, s_red, &st->sdeg);
@@ -821,7 +817,7 @@ void launch_round(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent
     if (ev) cudaEventRecord(ev[0], s);
     if (a.pairs) k_argmax<true><<<h->argmax_grid, kT, 0, s>>>(a);
     else k_argmax<false><<<h->argmax_grid, kT, 0, s>>>(a);
-    if (ev) launch_kept_degrees(h, a, s, ev, 0);
+    if (ev) launch_kept_degrees(h, a, s, ev);
     launch_win_kill(h, a, s, ev, 1);
 }
 
@@ -883,9 +879,9 @@ void launch_live_edges(const Handle *h, const RoundArgs &a, cudaStream_t s, int 
     k_live_edges<<<grid_for((uint64_t)std::max<int64_t>(h->m, 1), kT, h->sm_count, 8), kT, 0, s>>>(a, random);
 }
 
-void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev, int random) {
+void launch_kept_degrees(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEvent_t *ev) {
     cudaEventRecord(ev[5], s);  // the end of the argmax span
-    k_kept_degrees<<<grid_for((uint64_t)h->nregions * 32, kT, h->sm_count, 8), kT, 0, s>>>(a, random);
+    k_kept_degrees<<<grid_for((uint64_t)h->nregions * 32, kT, h->sm_count, 8), kT, 0, s>>>(a);
 }
 
 hm_status capture_chain(Handle *h, cudaGraph_t g, void (*capture)(Handle *, cudaStream_t, void *), void *ctx,

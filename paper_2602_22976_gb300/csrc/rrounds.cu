@@ -167,24 +167,6 @@ __global__ void __launch_bounds__(kT) k_rinit(RoundArgs a) {
     }
 }
 
-// Appends a region's staged winners to the round's list with one atomic
-// (one counter word for the whole GPU: an atomic per winning step would
-// serialise on it). Kept out of line: inlined into the earlier scan
-// kernel it changed the code of its main loop and cost 0.3-0.5 ms.
-__device__ __noinline__ void flush_winners(const RoundArgs &a, uint64_t base, uint32_t won) {
-    const int lane = threadIdx.x & 31;
-    uint32_t wb = 0;
-    if (lane == 0) wb = atomicAdd(&a.st->nwin, won);
-    wb = __shfl_sync(kFull, wb, 0);
-    __syncwarp();
-    for (uint32_t x = lane; x < won; x += 32) {
-        const uint64_t idx = (uint64_t)wb + x;
-        if (idx < a.win_cap) a.win[idx] = a.wstage[base + x];
-        else a.st->fault = 2;
-    }
-}
-
-
 constexpr int kFlatC = 32;                // round 1: consecutive entries a lane takes per chunk
 constexpr uint64_t kFlatW = 32 * kFlatC;  // round 1: entries per warp chunk
 constexpr int kFlatSpan = 192;            // round 1: a chunk's vertex offsets staged in shared memory up to this many
@@ -313,54 +295,87 @@ __global__ void __launch_bounds__(kT) k_rflat(RoundArgs a) {
 // Round 1's proposals: for every vertex with a list (the flat scan left its
 // largest key in rbest), T[v] is the edge of that key; the vertex counts
 // itself in that edge's P counter, and the count that completes the edge
-// makes it a winner. Winners are staged per region of vertices and
-// appended with one atomic. The vertices that proposed are listed (the
-// kept list, which the statistics of the profiled replay read).
+// makes it a winner. A flat grid-stride loop, two vertices a lane in
+// flight. Winners are staged in a per-warp shared buffer and appended to
+// the round's list with one atomic per kWinStage of them (a graph has
+// millions of winners in round 1: one atomic on the list counter per warp
+// step serialised the kernel). The proposers are counted (the vertices
+// kept for round 2).
+constexpr int kWinStage = 256;
+
+__device__ __forceinline__ void flush_staged(const RoundArgs &a, const int32_t *buf, uint32_t cnt) {
+    const int lane = threadIdx.x & 31;
+    uint32_t wb = 0;
+    if (lane == 0) wb = atomicAdd(&a.st->nwin, cnt);
+    wb = __shfl_sync(kFull, wb, 0);
+    for (uint32_t x = lane; x < cnt; x += 32) {
+        const uint64_t idx = (uint64_t)wb + x;
+        if (idx < a.win_cap) a.win[idx] = buf[x];
+        else a.st->fault = 2;
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kT) k_rpropose(RoundArgs a) {
     __shared__ unsigned long long s_red[kT / 32];
+    __shared__ int32_t s_win[kT / 32][kWinStage];
+    __shared__ unsigned int s_cnt;
     DevState *st = a.st;
-    int32_t *out = a.list1;
-    uint32_t *cnt_out = a.lcnt + a.nregions;
-    const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    const uint64_t warp = (blockIdx.x * (uint64_t)kT + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * kT) >> 5;
+    int32_t *wbuf = s_win[threadIdx.x >> 5];
+    uint32_t staged = 0;  // uniform in the warp
+    const uint64_t stride = (uint64_t)gridDim.x * kT;
     unsigned long long props = 0;
-    for (uint64_t g = warp; g < a.nregions; g += nwarps) {
-        const uint64_t base = g * a.region;
-        const int64_t left = a.n - (int64_t)base;
-        const uint32_t c = left <= 0 ? 0u : (uint32_t)(left < (int64_t)a.region ? left : (int64_t)a.region);
-        uint32_t won = 0, kept = 0;
-        for (uint32_t i0 = 0; i0 < c; i0 += 32) {
-            const uint32_t i = i0 + lane;
-            bool w = false, keep = false;
-            int32_t nb = -1;
-            const int32_t v = (int32_t)(base + i);
-            if (i < c) {
-                const unsigned long long best = a.rbest[v];
-                if (best != 0) {
-                    const int32_t e = edge_of_key(best);  // T[v], input id
-                    reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(e, 0);
-                    w = propose(a, e);
-                    if (w) nb = __ldg(a.jof + e);  // winners are listed by relabelled id
-                    keep = true;
-                    ++props;
-                }
+    for (uint64_t v0 = blockIdx.x * (uint64_t)kT * 2 + threadIdx.x;; v0 += 2 * stride) {
+        if (v0 - threadIdx.x >= (uint64_t)a.n) break;  // uniform in the block: no vertex left for it
+        unsigned long long best[2];
+        bool w[2] = {false, false};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t v = v0 + (uint64_t)u * kT;
+            best[u] = v < (uint64_t)a.n ? a.rbest[v] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (best[u] != 0) {
+                const uint64_t v = v0 + (uint64_t)u * kT;
+                const int32_t e = edge_of_key(best[u]);  // T[v], input id
+                reinterpret_cast<int2 *>(a.vrec + v)[0] = make_int2(e, 0);
+                w[u] = propose(a, e);
+                ++props;
             }
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (keep) out[base + kept + __popc(km & lt)] = v;
-            kept += __popc(km);
-            const unsigned wm = __ballot_sync(kFull, w);
-            if (w) a.wstage[base + won + __popc(wm & lt)] = nb;
-            won += __popc(wm);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const unsigned wm = __ballot_sync(kFull, w[u]);
+            if (staged + __popc(wm) > (uint32_t)kWinStage) {  // uniform
+                flush_staged(a, wbuf, staged);
+                staged = 0;
+            }
+            if (w[u]) wbuf[staged + __popc(wm & lt)] = __ldg(a.jof + edge_of_key(best[u]));  // listed by relabelled id
+            staged += __popc(wm);
+            __syncwarp();
         }
-        if (lane == 0) {
-            cnt_out[g] = kept;
-            if (kept) atomicAdd(&st->cnt[1], kept);
-        }
-        if (won) flush_winners(a, base, won);
     }
+    if (staged) flush_staged(a, wbuf, staged);
     block_add_u64(props, s_red, &st->proposals);
+    // the proposers are the vertices kept for round 2 (the round end reads
+    // cnt[1]): one 32-bit atomic a block
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    if (props) atomicAdd(&s_cnt, (unsigned int)props);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(&st->cnt[1], s_cnt);
+}
+
+// Profiled replay only, between round 1's timed spans: the sum of the
+// degrees of the vertices kept for round 2 (every vertex with a list, the
+// ones the flat scan gave a key), into the round's counter.
+__global__ void __launch_bounds__(kT) k_rdeg1(RoundArgs a) {
+    __shared__ unsigned long long s_red[kT / 32];
+    unsigned long long sum = 0;
+    for (int64_t v = blockIdx.x * (int64_t)kT + threadIdx.x; v < a.n; v += (int64_t)gridDim.x * kT)
+        if (a.rbest[v] != 0) sum += (unsigned long long)(a.voff[v + 1] - a.voff[v]);
+    block_add_u64(sum, s_red, &a.st->sdeg);
 }
 
 // Round 1's flat scan: the vertex whose list holds entry c * kFlatW, for
@@ -792,7 +807,10 @@ void launch_round1(const Handle *h, const RoundArgs &a, cudaStream_t s, cudaEven
     if (ev) cudaEventRecord(ev[0], s);
     k_rflat<<<h->rflat_grid, kT, 0, s>>>(a);
     k_rpropose<<<h->rpropose_grid, kT, 0, s>>>(a);
-    if (ev) launch_kept_degrees(h, a, s, ev, 1);
+    if (ev) {  // the end of the argmax span, then the untimed degree count
+        cudaEventRecord(ev[5], s);
+        k_rdeg1<<<grid_for((uint64_t)h->n, kT, h->sm_count, 8), kT, 0, s>>>(a);
+    }
     launch_win_kill_end(h, a, s, ev, 2);
 }
 
