@@ -197,9 +197,8 @@ def kernel_bytes(stats: np.ndarray, n: int, m: int, kappa: int = 0, random: bool
             if r == 0:
                 # round 1, vertex-driven: every list entry; per vertex its offsets
                 # and largest key written; proposal = key read, record write,
-                # counter word read + write; kept = list write; winner = its id
-                b["argmax"] += (row[ADV] * 8 + n * (8 + 8) + row[PROP] * (8 + 8 + 4 + 4)
-                                + row[NEXT] * 4 + row[WIN] * 4)
+                # counter word read + write; winner = its id
+                b["argmax"] += (row[ADV] * 8 + n * (8 + 8) + row[PROP] * (8 + 8 + 4 + 4) + row[WIN] * 4)
                 if pairs:  # winner: order, mask; winner pin: pin, matched flag
                     b["win"] += row[WIN] * (4 + 1 + 4) + row[WPIN] * (4 + 1)
                 else:      # winner: offset pair, order, mask; winner pin: pin, record
