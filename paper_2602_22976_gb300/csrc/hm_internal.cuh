@@ -150,7 +150,7 @@ struct RoundArgs {
     // re-randomised rounds only (rrounds.cu)
     float noise_scale;          // amplitude * 2^-24
     uint64_t noise_s0;          // SplitMix64 start state of the priority stream
-    const int2 *vadjE;          // vertex lists as {input edge id, bits(base priority)}
+    const int2 *vadjE;          // round 1's lists as {input edge id, bits(round-1 priority)}
     const int32_t *jof;         // input id -> j
     uint32_t *P2;               // round 1's proposal counters (32-bit words)
     int t_input;                // T[v] holds input edge ids (re-randomised rounds), not j
@@ -231,9 +231,10 @@ struct Handle {
     // re-randomised rounds (allocated on first use, rrounds.cu)
     float noise = 0.f;          // 0: fixed order; > 0: amplitude of the per-round noise
     float graph_noise = 0.f;    // amplitude exec_rand was built with
+    float r1_noise = -1.f;      // amplitude vadjE's round-1 priorities were computed for
     bool last_random = false;   // the last match ran re-randomised rounds
     int4 *vrecR = nullptr;      // round 1: {T[v], 0, list start, list length}
-    int2 *vadjE = nullptr;      // vertex lists as {input edge id, bits(base priority)} (built once)
+    int2 *vadjE = nullptr;      // round 1's lists as {input edge id, bits(round-1 priority)}
     int4 *erec = nullptr;       // edge records in j order (built once)
     int4 *elist0 = nullptr, *elist1 = nullptr;  // live edge lists of the edge rounds
     uint32_t *ecnt = nullptr;                   // their region lengths

@@ -14,9 +14,10 @@
 // formulations compute it, each where its cost is lowest.
 //
 // Round 1 (every edge live) is vertex-driven. The vertex lists, stored as
-// {input edge id e, bits(base_e)} pairs (vadjE), are read as one flat array
-// (flat_round1) with no random read at all; each vertex's largest key goes
-// to rbest. k_rpropose then makes every proposal (the P counter of Alg. 1,
+// {input edge id e, bits(p_1(e))} pairs (vadjE: round 1's priority of the
+// entry's edge, computed once per handle and amplitude, so the scan hashes
+// nothing), are read as one flat array (flat_round1) with no random read at
+// all; each vertex's largest key goes to rbest. k_rpropose then makes every proposal (the P counter of Alg. 1,
 // counted up by input id and packed with the edge's size, so one atomic
 // tells whether the count reached |e|), and the win and kill kernels of
 // rounds.cu finish the round: the winners' vertices are marked, and every
@@ -190,8 +191,6 @@ __device__ __forceinline__ void flat_round1(const RoundArgs &a, uint32_t *s_off)
     const uint32_t nwarps = (gridDim.x * (uint32_t)kT) >> 5;
     const uint32_t kappa = (uint32_t)a.kappa;
     const uint32_t nchunks = (uint32_t)((a.kappa + kFlatW - 1) / kFlatW);
-    const uint64_t cr = round_counter_base(a.noise_s0, 1);
-    const float scale = a.noise_scale;
     for (uint32_t c = warp; c < nchunks; c += nwarps) {  // uniform in the warp
         const uint32_t cb = c * (uint32_t)kFlatW;
         const uint32_t p0 = cb + (uint32_t)lane * kFlatC;
@@ -264,7 +263,9 @@ __device__ __forceinline__ void flat_round1(const RoundArgs &a, uint32_t *s_off)
                         cs = ce;
                         ce = vo(cur + 1);
                     }
-                const unsigned long long key = scan_key(cr, scale, (uint32_t)ev[u].x, __int_as_float(ev[u].y));
+                // the entry holds bits(p_1(e)): key_1(e) needs no hash here
+                const unsigned long long key = ((unsigned long long)(uint32_t)ev[u].y << 32) |
+                                               (unsigned long long)(0xFFFFFFFFu - (uint32_t)ev[u].x);
                 m = key > m ? key : m;
             }
         }
@@ -743,17 +744,25 @@ __global__ void __launch_bounds__(kT) k_erec(const int32_t *order, const int64_t
     }
 }
 
-// Lists as {input edge id, bits(base priority)} pairs, and the inverse of
-// the edge order (built once per handle).
-__global__ void __launch_bounds__(kT) k_map(const int32_t *order, const int32_t *vadj, const float *w, int64_t m,
-                                          uint64_t kappa, int2 *vadjE, int32_t *jof) {
-    const uint64_t stride = (uint64_t)gridDim.x * kT;
-    for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += stride) {
-        const int32_t e = __ldg(order + __ldg(vadj + i));
-        vadjE[i] = make_int2(e, __float_as_int(w ? __ldg(w + e) : 1.0f));
-    }
-    for (uint64_t j = blockIdx.x * (uint64_t)kT + threadIdx.x; j < (uint64_t)m; j += stride)
+// The inverse of the edge order (built once per handle).
+__global__ void __launch_bounds__(kT) k_jof(const int32_t *order, int64_t m, int32_t *jof) {
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT)
         jof[order[j]] = (int32_t)j;
+}
+
+// Round 1's lists as {input edge id e, bits(p_1(e))}: the round-1 priority
+// of every entry's edge, computed with scan_key's arithmetic (so round 1's
+// keys are bit for bit those the hash gives), once per handle and noise
+// amplitude. Round 1 then reads its keys instead of hashing every list
+// entry (an edge appears in the lists of all its pins).
+__global__ void __launch_bounds__(kT) k_r1keys(const int32_t *order, const int32_t *vadj, const float *w,
+                                             uint64_t kappa, uint64_t s0, float scale, int2 *vadjE) {
+    const uint64_t cr = round_counter_base(s0, 1);
+    for (uint64_t i = blockIdx.x * (uint64_t)kT + threadIdx.x; i < kappa; i += (uint64_t)gridDim.x * kT) {
+        const int32_t e = __ldg(order + __ldg(vadj + i));
+        const unsigned long long key = scan_key(cr, scale, (uint32_t)e, w ? __ldg(w + e) : 1.0f);
+        vadjE[i] = make_int2(e, (int32_t)(uint32_t)(key >> 32));
+    }
 }
 
 template <typename K>
@@ -874,12 +883,10 @@ hm_status build_graph_rand(Handle *h) {
 
 }  // namespace
 
-hm_status rand_prepare(Handle *h, cudaStream_t s) {
-    h->rflat_grid = (unsigned)(h->sm_count * fit_per_sm(k_rflat));
-    h->rpropose_grid = (unsigned)(h->sm_count * fit_per_sm(k_rpropose));
-    h->epush_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_epush<true>) : fit_per_sm(k_epush<false>)));
-    h->ewin_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_ewin<true>) : fit_per_sm(k_ewin<false>)));
-    if (h->vrecR) return HM_OK;
+namespace {
+
+// The mode's buffers and the maps built once per handle.
+hm_status alloc_rand(Handle *h, cudaStream_t s) {
     const uint64_t n = (uint64_t)h->n, m = (uint64_t)h->m;
     // regions of the edge lists: four per warp of the offer kernel's grid,
     // whole 32-record steps
@@ -909,8 +916,7 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
         k_rrec<<<grid_for(n, kT, h->sm_count, 16), kT, 0, s>>>(h->voff, h->n, h->vrecR);
     if (m) {
         const float *w = h->weighted ? h->weights : nullptr;
-        k_map<<<grid_for(std::max<uint64_t>(m, h->kappa), kT, h->sm_count, 16), kT, 0, s>>>(
-            h->order, h->vadj, w, h->m, h->kappa, h->vadjE, h->jof);
+        k_jof<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->m, h->jof);
         k_erec<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, w, h->m, h->graph ? 1 : 0,
                                                                h->erec);
         if (!h->graph)  // graphs count in bytes and need no sizes
@@ -924,6 +930,26 @@ hm_status rand_prepare(Handle *h, cudaStream_t s) {
             return cuda_fail(e, "edge id maps");
         }
     }
+    return HM_OK;
+}
+
+}  // namespace
+
+hm_status rand_prepare(Handle *h, cudaStream_t s) {
+    h->rflat_grid = (unsigned)(h->sm_count * fit_per_sm(k_rflat));
+    h->rpropose_grid = (unsigned)(h->sm_count * fit_per_sm(k_rpropose));
+    h->epush_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_epush<true>) : fit_per_sm(k_epush<false>)));
+    h->ewin_grid = (unsigned)(h->sm_count * (h->graph ? fit_per_sm(k_ewin<true>) : fit_per_sm(k_ewin<false>)));
+    hm_status st;
+    if (!h->vrecR && (st = alloc_rand(h, s)) != HM_OK) return st;
+    if (h->r1_noise != h->noise && h->kappa) {  // round 1's keys for this amplitude
+        k_r1keys<<<grid_for(h->kappa, kT, h->sm_count, 16), kT, 0, s>>>(
+            h->order, h->vadj, h->weighted ? h->weights : nullptr, h->kappa, splitmix64_first(h->seed),
+            h->noise * (1.0f / 16777216.0f), h->vadjE);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "round-1 keys");
+    }
+    h->r1_noise = h->noise;
     return HM_OK;
 }
 
@@ -1020,6 +1046,7 @@ void free_rand_buffers(Handle *h) {
     h->elist1 = nullptr;
     h->ecnt = nullptr;
     h->rmatch = nullptr;
+    h->r1_noise = -1.f;
     if (h->exec_rand) cudaGraphExecDestroy(h->exec_rand);
     h->exec_rand = nullptr;
 }
