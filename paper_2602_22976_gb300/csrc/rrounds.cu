@@ -420,11 +420,17 @@ __device__ __forceinline__ void offer(unsigned long long *slot, unsigned long lo
     if (kPairs || __ldcg(slot) < key) atomicMax(slot, key);
 }
 
-// Loads the pins of a small edge (size <= kSmall) into registers.
-__device__ __forceinline__ void load_small(const int32_t *__restrict__ pinsj, uint32_t start, uint32_t size,
-                                           int32_t (&pv)[kSmall]) {
+// The pins of a small edge (size <= kSmall) in registers. A graph's record
+// holds its two endpoints in place of {first pin, size}; a hypergraph's
+// pins are loaded from the edge CSR.
+template <bool kPairs>
+__device__ __forceinline__ void record_pins(const int32_t *__restrict__ pinsj, const int4 &rec, uint32_t size,
+                                            int32_t (&pv)[kSmall]) {
 #pragma unroll
-    for (int k = 0; k < kSmall; ++k) pv[k] = (uint32_t)k < size ? __ldg(pinsj + start + k) : 0;
+    for (int k = 0; k < kSmall; ++k) {
+        if (kPairs) pv[k] = k == 0 ? rec.z : (k == 1 ? rec.w : 0);
+        else pv[k] = (uint32_t)k < size ? __ldg(pinsj + (uint32_t)rec.z + k) : 0;
+    }
 }
 
 // Step 1 of round r >= 2 (see the file comment). Past the round cap the
@@ -467,17 +473,17 @@ __global__ void __launch_bounds__(kT) k_epush(RoundArgs a) {
             const bool ok = i < cnt;
             const int4 rec = nrec;
             if (i + 32 < cnt) nrec = in[base + i + 32];
-            const uint32_t start = (uint32_t)rec.z, size = ok ? (uint32_t)rec.w : 0u;
+            const uint32_t start = (uint32_t)rec.z, size = ok ? (kPairs ? 2u : (uint32_t)rec.w) : 0u;
             const bool big = size > (uint32_t)kSmall;
             bool live = ok;
             int32_t pv[kSmall];
             if (by_flag) {
                 live = ok && a.alive[rec.x] != 0;
-                if (live && !big) load_small(a.pinsj, start, size, pv);
+                if (live && !big) record_pins<kPairs>(a.pinsj, rec, size, pv);
                 if (live) nscan += size;
             } else {
                 if (ok && !big) {
-                    load_small(a.pinsj, start, size, pv);
+                    record_pins<kPairs>(a.pinsj, rec, size, pv);
                     bool any = false;
 #pragma unroll
                     for (int k = 0; k < kSmall; ++k)
@@ -611,13 +617,13 @@ __global__ void __launch_bounds__(kT) k_ewin(RoundArgs a) {
                 const uint32_t i = i0 + lane;
                 const bool ok = i < cnt;
                 const int4 rec = ok ? in[(uint64_t)g * a.eregion + i] : make_int4(0, 0, 0, 0);
-                const uint32_t start = (uint32_t)rec.z, size = ok ? (uint32_t)rec.w : 0u;
+                const uint32_t start = (uint32_t)rec.z, size = ok ? (kPairs ? 2u : (uint32_t)rec.w) : 0u;
                 const bool big = size > (uint32_t)kSmall;
                 const unsigned long long key = scan_key(cr, scale, (uint32_t)rec.x, __int_as_float(rec.y));
                 bool win = ok;
                 int32_t pv[kSmall];
                 if (ok && !big) {
-                    load_small(a.pinsj, start, size, pv);
+                    record_pins<kPairs>(a.pinsj, rec, size, pv);
 #pragma unroll
                     for (int k = 0; k < kSmall; ++k)
                         if ((uint32_t)k < size) {
@@ -733,14 +739,20 @@ __global__ void __launch_bounds__(kT) k_rrec(const int64_t *voff, int64_t n, int
 }
 
 // Every edge as {input id, bits(base priority), first pin, size}, in j order
-// (the input of round 2).
-__global__ void __launch_bounds__(kT) k_erec(const int32_t *order, const int64_t *eoffj, const float *w, int64_t m,
-                                           int graph, int4 *erec) {
+// (the input of round 2); a graph's edge as {input id, bits(base
+// priority), endpoint, endpoint}, so its rounds read no pins.
+__global__ void __launch_bounds__(kT) k_erec(const int32_t *order, const int64_t *eoffj, const int32_t *pinsj,
+                                           const float *w, int64_t m, int graph, int4 *erec) {
     for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
         const int32_t e = __ldg(order + j);
-        const int64_t b = graph ? 2 * j : eoffj[j];
-        const int64_t s = graph ? 2 : eoffj[j + 1] - b;
-        erec[j] = make_int4(e, __float_as_int(w ? __ldg(w + e) : 1.0f), (int32_t)(uint32_t)b, (int32_t)s);
+        const int32_t wb = __float_as_int(w ? __ldg(w + e) : 1.0f);
+        if (graph) {
+            const int2 p = __ldg(reinterpret_cast<const int2 *>(pinsj) + j);
+            erec[j] = make_int4(e, wb, p.x, p.y);
+        } else {
+            const int64_t b = eoffj[j];
+            erec[j] = make_int4(e, wb, (int32_t)(uint32_t)b, (int32_t)(eoffj[j + 1] - b));
+        }
     }
 }
 
@@ -917,8 +929,8 @@ hm_status alloc_rand(Handle *h, cudaStream_t s) {
     if (m) {
         const float *w = h->weighted ? h->weights : nullptr;
         k_jof<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->m, h->jof);
-        k_erec<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, w, h->m, h->graph ? 1 : 0,
-                                                               h->erec);
+        k_erec<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->pinsj, w, h->m,
+                                                               h->graph ? 1 : 0, h->erec);
         if (!h->graph)  // graphs count in bytes and need no sizes
             k_size_words<<<grid_for(m, kT, h->sm_count, 16), kT, 0, s>>>(h->order, h->eoffj, h->m, h->S32, h->S64);
         const uint64_t nchunks = (h->kappa + kFlatW - 1) / kFlatW;
