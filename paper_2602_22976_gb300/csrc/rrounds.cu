@@ -420,15 +420,25 @@ __device__ __forceinline__ void offer(unsigned long long *slot, unsigned long lo
     if (kPairs || __ldcg(slot) < key) atomicMax(slot, key);
 }
 
-// The pins of a small edge (size <= kSmall) in registers. A graph's record
-// holds its two endpoints in place of {first pin, size}; a hypergraph's
-// pins are loaded from the edge CSR.
+// An edge record is {input id, bits(base priority), first pin, size}, or,
+// for an edge of two pins, {input id, bits(base priority), pin, pin | 2^31}
+// (the pins in place: a negative last word; vertex ids are below 2^31).
+// A graph's records all have their pins in place (kPairs: known at compile
+// time, which keeps the other form out of its kernels).
+template <bool kPairs>
+__device__ __forceinline__ uint32_t record_size(const int4 &rec) {
+    return (kPairs || rec.w < 0) ? 2u : (uint32_t)rec.w;
+}
+
+// The pins of a small edge (size <= kSmall) in registers: in the record,
+// or loaded from the edge CSR.
 template <bool kPairs>
 __device__ __forceinline__ void record_pins(const int32_t *__restrict__ pinsj, const int4 &rec, uint32_t size,
                                             int32_t (&pv)[kSmall]) {
+    const bool in_place = kPairs || rec.w < 0;
 #pragma unroll
     for (int k = 0; k < kSmall; ++k) {
-        if (kPairs) pv[k] = k == 0 ? rec.z : (k == 1 ? rec.w : 0);
+        if (in_place) pv[k] = k == 0 ? rec.z : (k == 1 ? (rec.w & 0x7FFFFFFF) : 0);
         else pv[k] = (uint32_t)k < size ? __ldg(pinsj + (uint32_t)rec.z + k) : 0;
     }
 }
@@ -473,7 +483,7 @@ __global__ void __launch_bounds__(kT) k_epush(RoundArgs a) {
             const bool ok = i < cnt;
             const int4 rec = nrec;
             if (i + 32 < cnt) nrec = in[base + i + 32];
-            const uint32_t start = (uint32_t)rec.z, size = ok ? (kPairs ? 2u : (uint32_t)rec.w) : 0u;
+            const uint32_t start = (uint32_t)rec.z, size = ok ? record_size<kPairs>(rec) : 0u;
             const bool big = size > (uint32_t)kSmall;
             bool live = ok;
             int32_t pv[kSmall];
@@ -617,7 +627,7 @@ __global__ void __launch_bounds__(kT) k_ewin(RoundArgs a) {
                 const uint32_t i = i0 + lane;
                 const bool ok = i < cnt;
                 const int4 rec = ok ? in[(uint64_t)g * a.eregion + i] : make_int4(0, 0, 0, 0);
-                const uint32_t start = (uint32_t)rec.z, size = ok ? (kPairs ? 2u : (uint32_t)rec.w) : 0u;
+                const uint32_t start = (uint32_t)rec.z, size = ok ? record_size<kPairs>(rec) : 0u;
                 const bool big = size > (uint32_t)kSmall;
                 const unsigned long long key = scan_key(cr, scale, (uint32_t)rec.x, __int_as_float(rec.y));
                 bool win = ok;
@@ -738,21 +748,20 @@ __global__ void __launch_bounds__(kT) k_rrec(const int64_t *voff, int64_t n, int
     }
 }
 
-// Every edge as {input id, bits(base priority), first pin, size}, in j order
-// (the input of round 2); a graph's edge as {input id, bits(base
-// priority), endpoint, endpoint}, so its rounds read no pins.
+// Every edge's record (record_size), in j order: the input of round 2. An
+// edge of two pins (every edge of a graph) carries them, so the edge
+// rounds read no pins for it.
 __global__ void __launch_bounds__(kT) k_erec(const int32_t *order, const int64_t *eoffj, const int32_t *pinsj,
                                            const float *w, int64_t m, int graph, int4 *erec) {
     for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < m; j += (int64_t)gridDim.x * kT) {
         const int32_t e = __ldg(order + j);
         const int32_t wb = __float_as_int(w ? __ldg(w + e) : 1.0f);
-        if (graph) {
-            const int2 p = __ldg(reinterpret_cast<const int2 *>(pinsj) + j);
-            erec[j] = make_int4(e, wb, p.x, p.y);
-        } else {
-            const int64_t b = eoffj[j];
-            erec[j] = make_int4(e, wb, (int32_t)(uint32_t)b, (int32_t)(eoffj[j + 1] - b));
-        }
+        const int64_t b = graph ? 2 * j : eoffj[j];
+        const int64_t size = graph ? 2 : eoffj[j + 1] - b;
+        if (size == 2)
+            erec[j] = make_int4(e, wb, __ldg(pinsj + b), (int32_t)(0x80000000u | (uint32_t)__ldg(pinsj + b + 1)));
+        else
+            erec[j] = make_int4(e, wb, (int32_t)(uint32_t)b, (int32_t)size);
     }
 }
 
