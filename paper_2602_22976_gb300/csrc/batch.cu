@@ -12,6 +12,17 @@
 // All classes' loops are independent branches of one CUDA graph, so classes
 // in their latency-bound last rounds overlap the work of others. Each class
 // has its own launch shape, optionally picked by the autotuner.
+//
+// A class of small instances (every instance below kSmallClassPins pins) is
+// not run as a union round loop: a persistent kernel of one-block workers
+// takes its instances one at a time from a counter and matches each alone,
+// every round inside the block (the rounds of Sec. 3.1 written edge by edge:
+// every live edge folds its key into its vertices' slots with a 64-bit
+// atomicMax, edges holding the slot at all their vertices win, edges with a
+// matched vertex die), on the instance's part of the union's input arrays.
+// It writes the union's result mask and per-edge rounds, so the results are
+// read the same way for every class. The union handle is still built (its
+// validation and weights serve), but its round loop is not launched.
 #include "hm_internal.cuh"
 #include "exact_sum.cuh"
 
@@ -36,10 +47,31 @@ struct Member {            // one instance inside its class's union
     int64_t nv;            // its vertex count: local pins must be in [0, nv)
 };
 
+// One instance of a small class: its first union edge (its edges' offsets
+// are eoff_u[ub .. ub + m], absolute union pin positions), its first union
+// vertex, and its sizes.
+struct SmallInst {
+    int64_t ub, vb;
+    int32_t n, m;
+};
+
+constexpr int64_t kSmallClassPins = 1 << 16;          // a class is small when every instance is below this
+constexpr size_t kSmallScratchBytes = size_t(2) << 20;  // and one worker's working memory fits this
+constexpr int kSmallThreads = 1024;
+
 struct BatchClass {
     std::vector<int32_t> inst;  // member instances, ascending
     std::vector<Member> mem;
     Handle *h = nullptr;
+    // small classes: the union's input arrays (kept), the instance table,
+    // the workers' working memory
+    bool small = false;
+    int64_t *eoff_u = nullptr;
+    int32_t *pins_u = nullptr;
+    SmallInst *si = nullptr;
+    unsigned char *scratch = nullptr;
+    size_t scratch_per = 0;
+    unsigned grid = 0;
 };
 
 struct Batch {
@@ -106,6 +138,97 @@ __global__ void k_union_pins(const int32_t *__restrict__ pins, const Member *__r
     }
 }
 
+// Small classes: resets the instance counter and the class's status.
+__global__ void k_small_init(DevState *st) {
+    st->nwin = 0;
+    st->status = HM_OK;
+    st->fault = 0;
+    st->finished = 1;
+}
+
+__host__ __device__ __forceinline__ size_t small_align(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The key of an instance's edge e (instance-local id): weight bits, then the
+// smaller id first; unweighted, the seeded fmix32 priority of the local id
+// (the order hm_create gives the instance alone).
+__device__ __forceinline__ unsigned long long small_key(const float *w, uint32_t salt, int32_t e) {
+    if (w) return ((unsigned long long)__float_as_uint(w[e]) << 32) | (0xFFFFFFFFull - (uint32_t)e);
+    return (0x3F800000ull << 32) | fmix32((uint32_t)e ^ salt);
+}
+
+// Small classes: one-block workers, each matching whole instances taken from
+// a counter (st->nwin), every round inside the block. Working memory of a
+// worker: best (uint64[n]), matched (uint8[n]), alive (uint8[m]).
+__global__ void __launch_bounds__(kSmallThreads, 1)
+k_small_batch(const SmallInst *__restrict__ si, int32_t count, const int64_t *__restrict__ eoff_u,
+              const int32_t *__restrict__ pins_u, const float *__restrict__ w_u, uint32_t salt,
+              uint8_t *__restrict__ inM, int32_t *__restrict__ wround, unsigned char *__restrict__ scratch,
+              size_t per, DevState *st) {
+    __shared__ int32_t s_i;
+    unsigned char *my = scratch + (size_t)blockIdx.x * per;
+    const int t = threadIdx.x;
+    for (;;) {
+        if (t == 0) s_i = (int32_t)atomicAdd(&st->nwin, 1u);
+        __syncthreads();
+        const int32_t i = s_i;
+        __syncthreads();  // every thread has read s_i before it is rewritten
+        if (i >= count) break;  // uniform
+        const SmallInst q = si[i];
+        const int64_t *eo = eoff_u + q.ub;
+        const float *w = w_u ? w_u + q.ub : nullptr;
+        unsigned long long *best = reinterpret_cast<unsigned long long *>(my);
+        uint8_t *matched = my + small_align((size_t)q.n * 8);
+        uint8_t *alive = matched + small_align((size_t)q.n);
+        for (int32_t e = t; e < q.m; e += kSmallThreads) {
+            alive[e] = 1;
+            inM[q.ub + e] = 0;
+        }
+        for (int32_t v = t; v < q.n; v += kSmallThreads) matched[v] = 0;
+        __syncthreads();
+        int32_t rounds = 0;
+        for (;;) {
+            for (int32_t v = t; v < q.n; v += kSmallThreads) best[v] = 0ull;
+            __syncthreads();
+            int any = 0;
+            for (int32_t e = t; e < q.m; e += kSmallThreads) {
+                if (!alive[e]) continue;
+                any = 1;
+                const unsigned long long k = small_key(w, salt, e);
+                for (int64_t p = eo[e]; p < eo[e + 1]; ++p) atomicMax(&best[pins_u[p] - q.vb], k);
+            }
+            if (!__syncthreads_or(any)) break;
+            if (rounds >= q.m) {  // every round has a winner: never reached for valid input
+                if (t == 0) st->status = HM_ECUDA;
+                break;
+            }
+            ++rounds;
+            for (int32_t e = t; e < q.m; e += kSmallThreads) {
+                if (!alive[e]) continue;
+                const unsigned long long k = small_key(w, salt, e);
+                bool all = true;
+                for (int64_t p = eo[e]; p < eo[e + 1] && all; ++p) all = best[pins_u[p] - q.vb] == k;
+                if (all) {  // winners are vertex-disjoint: these writes never collide
+                    inM[q.ub + e] = 1;
+                    wround[q.ub + e] = rounds;
+                    alive[e] = 0;
+                    for (int64_t p = eo[e]; p < eo[e + 1]; ++p) matched[pins_u[p] - q.vb] = 1;
+                }
+            }
+            __syncthreads();
+            for (int32_t e = t; e < q.m; e += kSmallThreads) {
+                if (!alive[e]) continue;
+                for (int64_t p = eo[e]; p < eo[e + 1]; ++p)
+                    if (matched[pins_u[p] - q.vb]) {
+                        alive[e] = 0;
+                        break;
+                    }
+            }
+            __syncthreads();
+        }
+        __syncthreads();  // the block's working memory is reused by the next instance
+    }
+}
+
 __global__ void k_gather_rounds(const int32_t *__restrict__ idx, const int32_t *__restrict__ wround,
                                 const uint32_t *__restrict__ count, int32_t *__restrict__ out) {
     const uint32_t c = *count;
@@ -119,13 +242,18 @@ hm_status bad(const char *msg) {
 }
 
 void free_batch(Batch *b) {
-    for (auto &c : b->cls)
+    for (auto &c : b->cls) {
         if (c.h) {
             if (c.h->done) cudaEventSynchronize(c.h->done);
             if (c.h->cap_stream) cudaStreamSynchronize(c.h->cap_stream);
+        }
+        for (void *p : {(void *)c.eoff_u, (void *)c.pins_u, (void *)c.si, (void *)c.scratch})
+            if (p) cudaFree(p);
+        if (c.h) {
             free_handle_buffers(c.h);
             delete c.h;
         }
+    }
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->done) cudaEventDestroy(b->done);
     delete b;
@@ -160,6 +288,17 @@ hm_status build_class(Batch *b, BatchClass &c, const int64_t *eoff, const int32_
     }
     if (n_u > INT32_MAX || m_u > INT32_MAX || (uint64_t)k_u > 0xFFFFFFFFull)
         return bad("a size class of the batch exceeds 2^31-1 vertices or edges or 2^32-1 pins");
+    {
+        int64_t maxk = 0, maxn = 0, maxm = 0;
+        for (int k = 0; k < nmem; ++k) {
+            const int32_t i = c.inst[k];
+            maxk = std::max(maxk, b->kappa[i]);
+            maxn = std::max(maxn, b->n[i]);
+            maxm = std::max(maxm, b->m[i]);
+        }
+        c.scratch_per = small_align((size_t)maxn * 8) + small_align((size_t)maxn) + small_align((size_t)maxm);
+        c.small = maxk < kSmallClassPins && c.scratch_per <= kSmallScratchBytes;
+    }
     Member *d_mem = nullptr;
     int64_t *d_ub = nullptr, *d_pb = nullptr, *eoff_u = nullptr;
     int32_t *pins_u = nullptr;
@@ -204,6 +343,33 @@ hm_status build_class(Batch *b, BatchClass &c, const int64_t *eoff, const int32_
                 st = cuda_fail(e, "cudaEventCreate");
         }
     }
+    if (st == HM_OK && c.small) {
+        // the workers read the union's input arrays: keep them (they live as
+        // long as the batch), with the instance table and working memory
+        std::vector<SmallInst> si(nmem);
+        for (int k = 0; k < nmem; ++k) {
+            const int32_t i = c.inst[k];
+            si[k] = SmallInst{c.mem[k].ub, c.mem[k].vb, (int32_t)b->n[i], (int32_t)b->m[i]};
+        }
+        int per_sm = 0;  // resident workers per SM
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_batch, kSmallThreads, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        c.grid = (unsigned)std::min<int64_t>(nmem, (int64_t)sm_count * per_sm);
+        if ((e = cudaMalloc((void **)&c.si, si.size() * sizeof(SmallInst))) != cudaSuccess ||
+            (e = cudaMemcpyAsync(c.si, si.data(), si.size() * sizeof(SmallInst), cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaMalloc((void **)&c.scratch, std::max<size_t>(1, c.scratch_per * c.grid))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c.eoff_u, (size_t)(m_u + 1) * 8)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c.pins_u, (size_t)std::max<int64_t>(1, k_u) * 4)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(c.eoff_u, eoff_u, (size_t)(m_u + 1) * 8, cudaMemcpyDeviceToDevice, s)) !=
+                cudaSuccess ||
+            (k_u > 0 && (e = cudaMemcpyAsync(c.pins_u, pins_u, (size_t)k_u * 4, cudaMemcpyDeviceToDevice, s)) !=
+                            cudaSuccess))
+            st = cuda_fail(e, "batch small class");
+    }
     if (d_mem) cudaFreeAsync(d_mem, s);
     if (d_ub) cudaFreeAsync(d_ub, s);
     if (d_pb) cudaFreeAsync(d_pb, s);
@@ -214,13 +380,30 @@ hm_status build_class(Batch *b, BatchClass &c, const int64_t *eoff, const int32_
     return st;
 }
 
+// A small class's branch of the batch graph: counter reset, then the workers.
+void capture_small(Handle *h, cudaStream_t s, void *ctx) {
+    const BatchClass &c = *static_cast<const BatchClass *>(ctx);
+    k_small_init<<<1, 1, 0, s>>>(h->st);
+    k_small_batch<<<c.grid, kSmallThreads, 0, s>>>(c.si, (int32_t)c.inst.size(), c.eoff_u, c.pins_u,
+                                                    h->weighted ? h->weights : nullptr,
+                                                    (uint32_t)splitmix64_first(h->seed), h->inM, h->wround,
+                                                    c.scratch, c.scratch_per, h->st);
+}
+
 hm_status build_batch_graph(Batch *b) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
     hm_status st = HM_OK;
-    for (auto &c : b->cls)
-        if (st == HM_OK) st = add_match_to_graph(c.h, g);
+    for (auto &c : b->cls) {
+        if (st != HM_OK) break;
+        if (c.small) {
+            cudaGraphNode_t tail = nullptr;
+            st = capture_chain(c.h, g, capture_small, &c, &tail);
+        } else {
+            st = add_match_to_graph(c.h, g);
+        }
+    }
     if (st == HM_OK) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
