@@ -123,6 +123,11 @@ __global__ void __launch_bounds__(kT) k_p0(RoundArgs a, uint32_t *__restrict__ p
     }
 }
 
+// Requests the 16-byte line holding *p into L2 (no register is written).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 constexpr int kLaneSteps = 4;  // a lane walks at most 4 x 4 entries before its warp helps
 
 // First live entry of vadj[c, end) within kLaneSteps steps of four entries
@@ -445,10 +450,27 @@ __global__ void __launch_bounds__(kT, 6) k_argmax(RoundArgs a) {
         } else {
             count = cnt_in[g];
         }
+        // from round 2 on the list ids run two groups ahead, and the record
+        // of the next group's vertex is requested into L2 while this group
+        // walks (the id chain list -> record -> flag -> list is latency-bound
+        // once the rounds thin out)
+        int32_t vn1 = 0, vn2 = 0;
+        if (r > 1) {
+            vn1 = lane < count ? in[base + lane] : 0;
+            vn2 = 32u + lane < count ? in[base + 32 + lane] : 0;
+        }
         for (uint32_t i0 = 0; i0 < count; i0 += 32) {
             const uint32_t i = i0 + lane;
             const bool ok = i < count;
-            const int32_t v = ok ? (r == 1 ? (int32_t)(base + i) : in[base + i]) : 0;
+            int32_t v;
+            if (r == 1) {
+                v = ok ? (int32_t)(base + i) : 0;
+            } else {
+                v = ok ? vn1 : 0;
+                vn1 = vn2;
+                if (i + 32 < count) prefetch_l2(a.vrec + vn1);
+                vn2 = i + 64 < count ? in[base + i + 64] : 0;
+            }
             int32_t nb;
             const bool keep = argmax_vertex<kPairs>(a, r, ok, v, nb, adv);
             bool w = false;
