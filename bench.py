@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="large")
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10,
+                    help="end-to-end calls timed one by one after two untimed ones; the median is reported")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="default workload: leave out the batch sub-object (the batching workload at full size)")
@@ -288,6 +289,23 @@ def method_match_bytes(stats: np.ndarray) -> dict:
     a4 = (s[:, LED].sum() + s[:, NEXT].sum()) * 8
     return {"a1": float(a1), "a2": float(a2), "a3": float(a3), "a4": float(a4),
             "total": float(a1 + a2 + a3 + a4)}
+
+
+def timed_calls(call, k: int):
+    """End-to-end calls through the public API: two untimed ones, then k
+    timed one by one on the host clock (each ends with its result on the
+    host and a device synchronisation). Returns the median seconds, every
+    call's milliseconds and the last call's result."""
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize()
+    ts, out = [], None
+    for _ in range(max(k, 1)):
+        t0 = time.perf_counter()
+        out = call()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts)), [round(t * 1e3, 3) for t in ts], out
 
 
 def random_access_roofline(stats: np.ndarray, prof: dict, ra: dict, random: bool) -> dict | None:
@@ -856,17 +874,11 @@ def run_ours(args, world, rank, local):
                     m2.set_noise(args.noise)
                     m2.match()
                     return m2.result()
-            call()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.e2e_steps):
-                r2 = call()
-            torch.cuda.synchronize()
-            te = (time.perf_counter() - t0) / args.e2e_steps
+            te, tes, r2 = timed_calls(call, args.e2e_steps)
             assert r2.rounds == res.rounds and r2.count == res.count
             h2d = h.eoff.nbytes + h.pins.nbytes + (0 if h.weights is None else h.weights.nbytes)
             e2e = {"value": h.kappa * res.rounds / te, "unit": "pins/s", "ms_per_step": te * 1e3,
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 4 + 64),
+                   "ms_calls": tes, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 4 + 64),
                    "path": "hm_create + hm_set_noise + hm_match + hm_result"}
         elif args.e2e_steps > 0:
             pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -878,17 +890,11 @@ def run_ours(args, world, rank, local):
             call = lambda: hm.solve_host_ptrs(h.n, h.m, eoff_p.data_ptr(), pins_p.data_ptr(),
                                               None if w_p is None else w_p.data_ptr(), h.seed,
                                               flags, edges_p.data_ptr(), sh)
-            call()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.e2e_steps):
-                cnt, rnd, _w = call()
-            torch.cuda.synchronize()
-            te = (time.perf_counter() - t0) / args.e2e_steps
+            te, tes, (cnt, rnd, _w) = timed_calls(call, args.e2e_steps)
             assert rnd == res.rounds and cnt == res.count
             h2d = h.eoff.nbytes + h.pins.nbytes + (0 if h.weights is None else h.weights.nbytes)
             e2e = {"value": h.kappa * res.rounds / te, "unit": "pins/s", "ms_per_step": te * 1e3,
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 8 + 64)}
+                   "ms_calls": tes, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.count * 8 + 64)}
         cpu = None
         cpu_greedy = None
         parity = None
