@@ -296,14 +296,16 @@ def timed_calls(call, k: int):
     timed one by one on the host clock (each ends with its result on the
     host and a device synchronisation). Returns the median seconds, every
     call's milliseconds and the last call's result."""
+    import torch
+    sync = torch.cuda.synchronize if torch.cuda.is_available() else (lambda: None)
     for _ in range(2):
         call()
-    torch.cuda.synchronize()
+    sync()
     ts, out = [], None
     for _ in range(max(k, 1)):
         t0 = time.perf_counter()
         out = call()
-        torch.cuda.synchronize()
+        sync()
         ts.append(time.perf_counter() - t0)
     return float(np.median(ts)), [round(t * 1e3, 3) for t in ts], out
 

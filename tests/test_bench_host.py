@@ -123,3 +123,18 @@ def test_method_argmax_bytes_from_the_counters():
     stats[:, 9] = [100, 30, 2]     # their degree sums
     stats[:, 1] = 999              # other columns play no part
     assert bench.method_argmax_bytes(stats) == 24 * 15 + 8 * 132
+
+
+def test_end_to_end_calls_timed_one_by_one():
+    """The end-to-end leg: two untimed calls, then k timed ones; the median
+    of the per-call times is reported with every call's milliseconds."""
+    n = {"calls": 0}
+
+    def call():
+        n["calls"] += 1
+        return n["calls"]
+
+    med, ms, last = bench.timed_calls(call, 5)
+    assert n["calls"] == 7 and last == 7
+    assert len(ms) == 5 and all(t >= 0 for t in ms)
+    assert med == pytest.approx(float(np.median(ms)) / 1e3, abs=1e-5)
