@@ -117,8 +117,9 @@ hm_status hm_match(hm_handle *h, void *cuda_stream);
 
 /*
  * hm_set_round_cap - stop the loop after at most `cap` rounds (cap >= 1).
- * The default cap is m + 1, which no valid input reaches: under a strict
- * order the best live edge wins every round, so at most m rounds run.
+ * The loop of Sec. 3.1 runs while a live edge exists; the default cap is
+ * m + 1, which no valid input reaches: under a strict order the best live
+ * edge wins every round, so at most m rounds run.
  * Errors: HM_EINVAL.
  */
 hm_status hm_set_round_cap(hm_handle *h, int64_t cap);
@@ -157,15 +158,16 @@ hm_status hm_set_noise(hm_handle *h, float amplitude);
  * (no counterpart in the paper; the result never depends on it).
  *   set  HOST int32[4] or NULL: {least list entries one warp of the kill
  *        kernel takes (64..2^20), blocks per SM of the argmax, win and kill
- *        kernels (0 = as many as fit; the win kernel runs only in the
- *        re-randomised rounds)}; takes effect at the next hm_match
+ *        kernels of the fixed order (0 = as many as fit)}; takes effect at
+ *        the next hm_match
  *   get  HOST int32[4] or NULL: the config in force
  * Errors: HM_EINVAL.
  */
 hm_status hm_launch_config(hm_handle *h, const int32_t *set, int32_t *get);
 
 /*
- * hm_autotune - pick the launch shape of this handle by measurement: a
+ * hm_autotune - pick the launch shape of this handle by measurement (no
+ * counterpart in the paper; the result never depends on it): a
  * coordinate-descent search over the least kill slice per warp and the blocks per SM
  * of the three round kernels, each candidate timed as the median of three
  * hm_match graph launches (CUDA events on `cuda_stream`). Leaves the best
@@ -194,13 +196,15 @@ hm_status hm_result(hm_handle *h, int32_t *edges_out, int64_t *count_out,
 
 /*
  * hm_result_device - enqueue on `cuda_stream` a copy of the membership mask
- * of the last match into DEVICE uint8[m] `in_matching` (1 = e in M), input
- * edge numbering. Does not wait. Errors: HM_EINVAL, HM_ECUDA.
+ * of the last match into DEVICE uint8[m] `in_matching` (1 = e in M, the
+ * matching of Sec. 2.1), input edge numbering. Does not wait.
+ * Errors: HM_EINVAL, HM_ECUDA.
  */
 hm_status hm_result_device(hm_handle *h, uint8_t *in_matching, void *cuda_stream);
 
 /*
- * hm_round_stats - per-round counters of the last match (waits for it).
+ * hm_round_stats - per-round counters of the last match (waits for it): the
+ * work of every round, whose sum over rounds Sec. 4.3 bounds by O(kappa).
  * For round r (0-based, r < min(rounds_cap, 4096)) row r of HOST
  * int64[max_rounds][HM_STATS_COLS] receives the counters below. In the
  * re-randomised rounds (hm_set_noise) rounds from the second on are
@@ -249,7 +253,8 @@ hm_status hm_round_stats(hm_handle *h, int64_t *stats, int32_t max_rounds, int32
 hm_status hm_vertex_state(hm_handle *h, int32_t *best_edge_out);
 
 /*
- * hm_profile_match - run one match with the rounds driven from the host,
+ * hm_profile_match - run one match (Sec. 3.1 rounds, as hm_match) with the
+ * rounds driven from the host,
  * one launch per kernel with a CUDA event pair around every launch on
  * `cuda_stream`, and report per kernel kind k (HM_K_*):
  *   ms_out[k]        summed device time of its launches (CUDA events)
@@ -262,9 +267,11 @@ hm_status hm_vertex_state(hm_handle *h, int32_t *best_edge_out);
  */
 #define HM_K_INIT    0  /* per-match state reset */
 #define HM_K_ARGMAX  1  /* a1: vertex argmax (cursor advance) + proposals; in the
-                           fixed order also a2 (one kernel) */
-#define HM_K_WIN     2  /* a2: winners join M, their vertices are marked (its own
-                           kernel only in the re-randomised rounds) */
+                           fixed order also a2's win test (the countdown that
+                           reaches 0); the edge rounds' offers */
+#define HM_K_WIN     2  /* a2: winners join M, their vertices are marked (the
+                           fixed order also emits the kill ranges here); the
+                           edge rounds' win test */
 #define HM_K_KILL    3  /* a3: deactivate edges of newly matched vertices, and a4 */
 #define HM_K_ROUND   4  /* a4: round bookkeeping, termination test: part of the
                            kill kernel, so no launches and no time of its own */
@@ -273,14 +280,17 @@ hm_status hm_profile_match(hm_handle *h, void *cuda_stream, double *ms_out, int6
                            double *round_ms_out, int32_t max_rounds);
 
 /*
- * hm_create_ms - device time of the hm_create phases of this handle
- * (CUDA events): [0] validation, [1] priority sort, [2] edge relabel,
+ * hm_create_ms - device time of the hm_create phases of this handle (the
+ * preprocessing Sec. 5.1 leaves out of the match time; CUDA events):
+ * [0] validation, [1] priority sort, [2] edge relabel,
  * [3] vertex CSR build, [4] total. HOST double[5]. Errors: HM_EINVAL.
  */
 hm_status hm_create_ms(hm_handle *h, double *ms_out);
 
 /*
- * hm_solve_host - one call from HOST buffers to HOST result: copies eoff,
+ * hm_solve_host - one call from HOST buffers to HOST result (the problem of
+ * Sec. 2.1 solved by the rounds of Sec. 3.1, load and transfer included):
+ * copies eoff,
  * pins, weights (host memory; pinned memory gives full link bandwidth) to
  * the device on `cuda_stream`, runs hm_create + hm_match + hm_result and
  * frees everything. From 4M pins on, the pins cross in chunks on a second
@@ -346,11 +356,16 @@ hm_status hm_match_noalloc(int64_t n, int64_t m, const int64_t *eoff, const int3
  *   seed, flags  as hm_create, plus HM_AUTOTUNE and HM_ONE_CLASS
  * Instances are grouped into size classes by kappa (factors of four); each
  * class is matched as the disjoint union of its instances, and all classes
- * are independent branches of one CUDA graph. Every instance gets exactly
+ * are independent branches of one CUDA graph. A class whose every instance
+ * has fewer than 65,536 pins (and whose largest instance needs at most 2 MiB
+ * of working memory, 9n + m bytes) is instead one persistent kernel of
+ * one-block workers, each taking instances from a counter and running all
+ * of an instance's rounds inside the block. Every instance gets exactly
  * the matching and round count it would get from its own hm_create/hm_match
  * (unweighted priorities use instance-local edge ids). With HM_AUTOTUNE each
- * class's launch shape is chosen by hm_autotune's search. The inputs may be
- * freed once the call returns (it synchronises `cuda_stream`).
+ * union class's launch shape is chosen by hm_autotune's search (a class of
+ * one-block workers keeps the default shape, which it does not use). The
+ * inputs may be freed once the call returns (it synchronises `cuda_stream`).
  * Errors: HM_EINVAL (as hm_create, per instance; a class beyond 2^31-1
  * vertices or edges or 2^32-1 pins), HM_ENOMEM, HM_ECUDA.
  */
@@ -359,6 +374,7 @@ hm_status hm_batch_create(hm_batch **out, int32_t count, const int64_t *n, const
                           uint32_t flags, void *cuda_stream);
 
 /* hm_batch_match - enqueue the whole batch (one graph launch); does not wait.
+ * The batch calls have no counterpart in the paper (see hm_batch_create).
  * Errors: HM_EINVAL, HM_EBUSY (running on another stream), HM_ECUDA. */
 hm_status hm_batch_match(hm_batch *b, void *cuda_stream);
 
@@ -403,7 +419,8 @@ void hm_batch_destroy(hm_batch *b);
 hm_status hm_server_create(hm_server **out, int32_t slots, uint64_t hbm_budget_bytes);
 
 /*
- * hm_server_submit - queue one request: HOST eoff/pins/weights as for
+ * hm_server_submit - queue one request (the server calls, like
+ * hm_server_create, have no counterpart in the paper): HOST eoff/pins/weights as for
  * hm_solve_host (pinned host memory gives full copy bandwidth). The caller
  * keeps the three arrays unchanged until hm_server_wait returns for the
  * ticket. Returns at once with a ticket (> 0).
@@ -431,7 +448,8 @@ hm_status hm_server_stats(hm_server *s, int64_t *stats_out);
  * free the server (results not yet collected are dropped). NULL is a no-op. */
 void hm_server_destroy(hm_server *s);
 
-/* hm_last_error - message of the last failure on this thread ("" if none). */
+/* hm_last_error - message of the last failure on this thread ("" if none; no
+ * counterpart in the paper, nor has any of the lifetime calls). */
 const char *hm_last_error(void);
 
 /* hm_destroy - wait for outstanding work of the handle and free it. NULL is a no-op. */

@@ -531,7 +531,7 @@ hm_status hm_batch_create(hm_batch **out, int32_t count, const int64_t *n, const
             free_batch(b);
             return st;
         }
-        if (flags & HM_AUTOTUNE) {
+        if ((flags & HM_AUTOTUNE) && !c.small) {  // a small class's workers have no launch shape to tune
             LaunchConfig best;
             double ms = 0;
             if ((st = autotune(c.h, s, &best, &ms)) != HM_OK) {
