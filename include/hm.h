@@ -331,8 +331,8 @@ hm_status hm_solve_host(int64_t n, int64_t m, const int64_t *eoff, const int32_t
  * e.g. n = 500,000 and m = 3,000,000. Larger inputs return HM_EINVAL with a
  * message naming the size; use hm_create/hm_match for them.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. All calls share the one array and every call
+ * (cudaGetSymbolAddress, with that device current). All calls share the
+ * one array and every call
  * clears the parts it uses, so calls whose kernels overlap on the GPU
  * (different streams, or several host threads) race and corrupt each other;
  * serialise them. Errors returned directly: HM_EINVAL (sizes, flags, NULL or
