@@ -469,7 +469,7 @@ PAPER_CONTEXT = {
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, world, rank):
-    """The CPU oracle (this project's reference) on the machine's host cores, on
+    """The CPU oracle (this project's reference) on this machine's host cores, on
     the bench's own instance (the full workload where it has one; the batch
     and serve workloads use a sample of their generator), one oracle run per
     step. Under torchrun only rank 0 runs it."""
