@@ -70,6 +70,32 @@ def test_batch_one_class(weighted):
         check_against_oracle(hs, b.result())
 
 
+@pytest.mark.parametrize("weighted", [True, False])
+def test_batch_one_class_of_small_instances(weighted):
+    """HM_ONE_CLASS over instances all below 65,536 pins (the server's groups
+    of small requests): the class runs on the one-block workers, and every
+    instance still gets its solo result; a second launch repeats it. One
+    member has 300,000 isolated vertices: its working memory (9n + m bytes)
+    is above a worker's 2 MiB, so that class runs as a union instead."""
+    rng = np.random.default_rng(7 if weighted else 8)
+    hs = []
+    for i in range(60):
+        n = int(rng.integers(10, 3000))
+        h = synth.generate(n, 2 * n, kmin=1, kmax=12, weighted=weighted, seed=700 + i)
+        h.seed = 2
+        hs.append(h)
+    with hmlib.Batch(hs, one_class=True) as b:
+        b.match()
+        check_against_oracle(hs, b.result())
+        b.match()
+        check_against_oracle(hs, b.result())
+    big = synth.generate(300_000, 200, kmin=2, kmax=4, weighted=weighted, seed=799)
+    big.seed = 2
+    with hmlib.Batch(hs[:5] + [big], one_class=True) as b:
+        b.match()
+        check_against_oracle(hs[:5] + [big], b.result())
+
+
 def test_batch_degenerate_members():
     hs = [synth.from_edges(5, [], []),
           synth.from_edges(3, [[0, 1, 2]], [0.5]),
