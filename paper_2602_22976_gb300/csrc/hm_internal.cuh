@@ -67,7 +67,7 @@ constexpr int kMinKillChunk = 64;    // smallest kill slice (entries per warp) a
 
 // Launch shape of the round kernels; the autotuner picks it per handle.
 struct LaunchConfig {
-    int kill_chunk = 256;  // least list entries a warp of the kill step takes
+    int kill_chunk = 64;   // least list entries a warp of the kill step takes
     int argmax_bpsm = 0;   // blocks per SM of k_argmax (0 = all that fit)
     int win_bpsm = 0;      // blocks per SM of k_win
     int kill_bpsm = 0;     // blocks per SM of k_kill

@@ -122,7 +122,7 @@ def test_single_handle_autotune_and_config():
     h = synth.large(seed=4, n=200_000, m=400_000)
     o = oracle.match(h)
     with hmlib.Matcher.from_hypergraph(h) as mt:
-        assert mt.launch_config() == (256, 0, 0, 0)
+        assert mt.launch_config() == (64, 0, 0, 0)
         for cfg in [(64, 2, 2, 2), (1024, 0, 4, 0), (128, 1, 0, 4)]:
             assert mt.launch_config(cfg) == cfg
             mt.match()
