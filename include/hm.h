@@ -159,7 +159,7 @@ hm_status hm_set_noise(hm_handle *h, float amplitude);
  *   set  HOST int32[4] or NULL: {least list entries one warp of the kill
  *        kernel takes (64..2^20), blocks per SM of the argmax, win and kill
  *        kernels of the fixed order (0 = as many as fit)}; takes effect at
- *        the next hm_match
+ *        the next hm_match. A new handle starts at {64, 0, 0, 0}.
  *   get  HOST int32[4] or NULL: the config in force
  * Errors: HM_EINVAL.
  */
