@@ -138,3 +138,69 @@ def test_end_to_end_calls_timed_one_by_one():
     assert n["calls"] == 7 and last == 7
     assert len(ms) == 5 and all(t >= 0 for t in ms)
     assert med == pytest.approx(float(np.median(ms)) / 1e3, abs=1e-5)
+
+
+def test_kernel_bytes_fixed_order_from_the_counters():
+    """This design's element bytes per kernel kind, fixed order, hypergraph,
+    16-bit counters: the per-unit table of the design written out by hand
+    for two rounds."""
+    ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT = range(8)
+    stats = np.zeros((2, 12), dtype=np.int64)
+    stats[0, [ACT, PROP, WIN, WPIN, KILL, ITEM, NEXT]] = [100, 90, 10, 40, 300, 30, 80]
+    stats[1, [ACT, ADV, PROP, WIN, WPIN, KILL, ITEM, NEXT]] = [80, 50, 20, 5, 15, 60, 12, 0]
+    b = bench.kernel_bytes(stats, n=100, m=200, random=False, p16=True, pairs=False)
+    assert b["init"] == 200 * (1 + 1 + 2 * 2)
+    # round 1: first entry + record write per vertex, P read + write per
+    # proposal, list write per kept vertex; every round: 12 per winner
+    argmax = (100 * 12 + 90 * 4 + 80 * 4) + (80 * 21 + 50 * 5 + 20 * 12 + 0) + 12 * (10 + 5)
+    assert b["argmax"] == argmax
+    # winner 21 + 4 (list), winner pin 28, kill range 8
+    assert b["win"] == (10 * 25 + 40 * 28 + 30 * 8) + (5 * 25 + 15 * 28 + 12 * 8)
+    # kill range read 8, killed entry 5
+    assert b["kill"] == (30 * 8 + 300 * 5) + (12 * 8 + 60 * 5)
+
+
+def test_random_access_roofline_from_the_counters():
+    """The time each kernel's random accesses take at the measured rates:
+    k_argmax one flag load per active vertex and skipped entry from round 2
+    on plus one returning atomic per proposal; k_kill one store per target
+    in round 1 and one load per target later; over the kernel's time."""
+    stats = np.zeros((3, 12), dtype=np.int64)
+    stats[:, 0] = [1000, 400, 100]     # active vertices
+    stats[:, 1] = [0, 800, 300]        # skipped entries
+    stats[:, 2] = [900, 200, 50]       # proposals
+    stats[:, 5] = [5000, 2000, 600]    # kill entries
+    ra = {"load1B": 100.0, "store1B": 50.0, "atomic4B": 25.0}  # 1e9 per second
+    prof = {"argmax": (0.001, 3), "kill": (0.0005, 3)}          # ms, launches
+    r = bench.random_access_roofline(stats, prof, ra, random=False)
+    argmax_s = (400 + 100 + 800 + 300) / 100e9 + (900 + 200 + 50) / 25e9
+    kill_s = (2000 + 600) / 100e9 + 5000 / 50e9
+    assert r["argmax"]["bound_ms"] == pytest.approx(argmax_s * 1e3)
+    assert r["argmax"]["frac"] == pytest.approx(argmax_s * 1e3 / 0.001)
+    assert r["kill"]["bound_ms"] == pytest.approx(kill_s * 1e3)
+    assert r["kill"]["frac"] == pytest.approx(kill_s * 1e3 / 0.0005)
+    assert bench.random_access_roofline(stats, prof, ra, random=True) is None
+
+
+def test_kernel_bytes_rerandomised_from_the_counters():
+    """Re-randomised rounds, hypergraph: round 1 is the flat scan, the
+    proposals, the win and the kill; later rounds are the edge rounds
+    (records in and out, the live pins' offers, the win test and the whole
+    clear of the other slot buffer), written out by hand for three rounds."""
+    ADV, PROP, WIN, WPIN, KILL, ITEM, LIVE, LEDGES = 1, 2, 3, 4, 5, 6, 8, 10
+    n, m = 100, 200
+    stats = np.zeros((3, 12), dtype=np.int64)
+    stats[0, [ADV, PROP, WIN, WPIN, KILL, ITEM]] = [1000, 90, 10, 40, 300, 30]
+    stats[1, [ADV, WIN, WPIN, LIVE, LEDGES]] = [600, 8, 20, 600, 120]
+    stats[2, [ADV, WIN, WPIN, LIVE, LEDGES]] = [90, 3, 6, 50, 15]
+    b = bench.kernel_bytes(stats, n=n, m=m, random=True, p16=True, pairs=False)
+    assert b["init"] == m * (1 + 4 + 4 + 1) + n * (1 + 8 + 8)
+    argmax = 1000 * 8 + n * 16 + 90 * 24 + 10 * 4                   # round 1
+    argmax += m * 16 + m + 0 + 120 * 16 + 600 * (4 + 8)              # round 2: every record and its flag
+    argmax += 120 * 16 + 90 * 5 + 15 * 16 + 50 * 8                  # round 3: round 2's live edges
+    assert b["argmax"] == argmax
+    win = 10 * 25 + 40 * 28 + 30 * 8                                 # round 1
+    win += 120 * 16 + 600 * 12 + 8 + 20 + 8 * n                      # round 2
+    win += 15 * 16 + 50 * 12 + 3 + 6 + 8 * n                         # round 3
+    assert b["win"] == win
+    assert b["kill"] == 30 * 8 + 300 * 9
