@@ -1,7 +1,7 @@
 """CPU oracle for locally-maximal hypergraph matching - TEST INFRASTRUCTURE.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package. The CUDA path never does, and this
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg and
+reference arm of ``bench.py`` may import this package. The CUDA path never does, and this
 package never imports the CUDA path: the two share no code.
 
 The arithmetic is in ``oracle.c`` (plain sequential C, compiled with gcc on

@@ -4,8 +4,8 @@
  * Reinstaedtler, Schulz, Sitchinava, Walliser).
  *
  * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
- * benchmark's CPU-baseline leg may load this library. It shares no code,
- * header, table or helper with the CUDA path.
+ * benchmark's CPU-baseline leg and reference arm may load this library. It
+ * shares no code, header, table or helper with the CUDA path.
  *
  * What it computes (Sec. 3.1 "Sequential Algorithm", Alg. 1 and Alg. 3):
  * rounds; in each round every vertex determines its highest-priority live
